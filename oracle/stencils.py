@@ -1,0 +1,380 @@
+"""Support regions, constrained fits and modified stencils (oracle).
+
+TEST INFRASTRUCTURE ONLY -- see ``oracle/__init__.py``.
+
+Paper sections followed, in the paper's order:
+1. Hyperspherical support of radius r around the expansion point, starting at
+   r = (M+1)/2 ("Constructing Finite-Difference Approximations", support
+   figure paragraph).
+2. Interior points in the support, minus those with a boundary point inside
+   their 2 eta-sided box; boundary points in the support carry one row per
+   boundary condition (Eq. of the BC dot product; general boundary linear
+   system).
+3. rank(A) must equal the number of basis terms; otherwise enlarge the support,
+   and as a last resort lower the basis order (rank paragraph; order-reduction
+   paragraph; 3D first-order example).
+4. delta = A^+ [f(X); g] with the Moore-Penrose pseudoinverse; exterior values
+   f~(X_e) = B A^+ [f(X); g]; with g = 0 the forcing columns drop out
+   ("Reconciliation with the Interior Numerical Discretization"; example
+   geometry).
+5. The interior stencil with exterior values replaced by the extrapolants gives
+   the modified operator (modified-stencil equation).  For the Laplacian all
+   axes share the expansion point, so the per-axis modified operators are
+   summed into one row (the Laplacian is the sum of per-dimension second
+   derivative operators, 2nd-order application section).
+6. Multiple fields: block rows, coupled by BC rows that span several fields
+   (multi-field section; particle-velocity free surface; appendix).
+
+A modified row is returned as the *correction* to the standard stencil:
+    L_mod f(x0) = sum_{interior axial} w_k f(x0 + k e_a) + sum_j c_j f(X_j)
+with c = ((A^+)^T u)[interior rows], u = sum_e w_e a(x_e - x0).  The first sum
+is the standard stencil with exterior values set to zero, which is what the
+propagators apply everywhere.
+
+Readings of the paper used here (the paper is silent or ambiguous):
+* support membership |x - x0|_2 <= r is decided exactly (positions are
+  half-integers in grid units, so 4|x - x0|^2 and 4 r^2 are integers);
+* boundary points are in the support if |x_b - x0|^2 <= r^2 + 1e-9;
+* r grows by 0.5 up to r0 + 3; then the basis order drops by 2 (down to 2);
+* rank test: sigma_min > rank_tol * sigma_max of A (SVD), and A has at least
+  as many rows as columns;
+* expansion point: the stencil centre (2nd-order form); the node receiving the
+  derivative (staggered form);
+* basis order of the extrapolants: min(M, 4) by default (``Opts.ib_order``).
+  The paper demonstrates order 4 only and allows a lower basis order than the
+  interior discretisation (order-reduction paragraph).  With an order-8 (or
+  order-6) basis the order-8 schemes grow exponentially on a seeded sinusoid
+  within 2000 steps, while the order-4 basis stays bounded.
+"""
+import math
+import itertools
+
+import numpy as np
+
+from . import taylor
+from .geometry import BoundaryPoints, in_array, logical_shape, value
+
+
+class RankError(RuntimeError):
+    """A node could not be constrained at the largest radius and lowest order."""
+
+
+class Opts:
+    def __init__(self, M, eta_p=0.5, eta_v=0.0, radius=0.0, growth=3.0,
+                 min_order=2, rank_tol=1e-10, ib_order=0):
+        self.M = int(M)
+        # basis order of the extrapolants (<= M); 0 selects min(M, 4)
+        self.ib_order = int(ib_order) if ib_order else min(int(M), 4)
+        self.eta_p = float(eta_p)
+        self.eta_v = float(eta_v)
+        self.radius = float(radius)
+        self.growth = float(growth)
+        self.min_order = int(min_order)
+        self.rank_tol = float(rank_tol)
+
+
+class Field:
+    """One unknown field of the fit: node j sits at j + shift (grid units)."""
+
+    def __init__(self, mask, shift, eta):
+        self.mask = mask
+        self.shift = np.asarray(shift, dtype=np.float64)
+        self.eta = float(eta)
+
+
+_SUPPORT_CACHE = {}
+
+
+def _support_offsets(frac, r):
+    """Offsets o (integer tuples) with |o - frac|_2 <= r, exact in quarter units,
+    sorted by distance then array order; frac in {-1/2, 0, 1/2}^d."""
+    key = (frac, r)
+    hit = _SUPPORT_CACHE.get(key)
+    if hit is not None:
+        return hit
+    d = len(frac)
+    four_r2 = int(math.floor(4.0 * r * r + 1e-9))
+    R = int(math.ceil(r)) + 1
+    out = []
+    for off in itertools.product(range(-R, R + 1), repeat=d):
+        q = sum(int(round(2.0 * (o - f))) ** 2 for o, f in zip(off, frac))
+        if q <= four_r2:
+            out.append((q, tuple(reversed(off)), off))
+    out.sort()
+    res = [o for _, _, o in out]
+    _SUPPORT_CACHE[key] = res
+    return res
+
+
+def support_nodes(xi0, shift, r, lshape):
+    """In-array nodes j of a field with |j + shift - xi0|_2 <= r, sorted by
+    distance, then by array-order index."""
+    base = [int(round(x - s)) for x, s in zip(xi0, shift)]
+    frac = tuple(float(x - s - b) for x, s, b in zip(xi0, shift, base))
+    out = []
+    for off in _support_offsets(frac, float(r)):
+        j = tuple(b + o for b, o in zip(base, off))
+        if in_array(j, lshape):
+            out.append(j)
+    return out
+
+
+def fit(xi0, fields, bps, bc_rows_fn, E, opts, lshape):
+    """Constrained extrapolation fit at expansion point xi0.
+
+    fields     : list of Field
+    bc_rows_fn : order -> BC template (``taylor.bc_templates_*``): rows of
+                 per-field (normal axis, operator) terms
+    E          : list of (field index, exterior position, standard weight)
+    Returns (support, c, info): support = [(field, node)], c = correction
+    weights of the modified operator on those nodes.
+    """
+    xi0 = np.asarray(xi0, dtype=np.float64)
+    d = len(xi0)
+    nf = len(fields)
+    for Mp in range(opts.ib_order, opts.min_order - 1, -2):
+        idx = taylor.multi_indices(d, Mp)
+        T = len(idx)
+        if opts.radius > 0 and Mp == opts.ib_order:
+            r0 = opts.radius
+        else:
+            r0 = (Mp + 1) / 2.0
+        for g in range(int(round(opts.growth / 0.5)) + 1):
+            r = r0 + 0.5 * g
+            sup = []
+            for f, F in enumerate(fields):
+                for j in support_nodes(xi0, F.shift, r, lshape):
+                    if not value(F.mask, j):
+                        continue
+                    pos = np.array(j, dtype=np.float64) + F.shift
+                    if bps.eta_excluded(pos, F.eta):
+                        continue
+                    sup.append((f, j, pos))
+            blist = bps.within(xi0, r)
+            rows = []
+            for f in range(nf):
+                P = [pos - xi0 for ff, _, pos in sup if ff == f]
+                if P:
+                    blk = np.zeros((len(P), nf * T))
+                    blk[:, f * T:(f + 1) * T] = taylor.basis_rows(np.array(P), idx)
+                    rows.extend(blk)
+            if blist:
+                rows.extend(taylor.template_rows(bc_rows_fn(Mp), bps.xb[blist] - xi0,
+                                                 bps.normal[blist], idx, nf))
+            if len(rows) < nf * T:
+                continue
+            A = np.array(rows)
+            sv = np.linalg.svd(A, compute_uv=False)
+            if not sv[-1] > opts.rank_tol * sv[0]:
+                continue
+            u = np.zeros(nf * T)
+            for f, xe, w in E:
+                u[f * T:(f + 1) * T] += w * taylor.basis_row(np.asarray(xe, dtype=np.float64) - xi0, idx)
+            y = np.linalg.pinv(A).T @ u
+            info = dict(radius=r, order=Mp, n_bp=len(blist), n_rows=A.shape[0],
+                        n_int=len(sup), cond=float(sv[0] / sv[-1]), A=A, u=u, y=y)
+            return [(f, j) for f, j, _ in sup], y[:len(sup)], info
+    raise RankError("node at %s unconstrained" % (tuple(xi0),))
+
+
+# ---------------------------------------------------------------------------
+# 2nd-order form: merged modified Laplacian
+# ---------------------------------------------------------------------------
+def _shifted(mask, axis_arr, k):
+    """out[i] = mask[i + k] along array axis (False outside the array)."""
+    out = np.zeros_like(mask)
+    n = mask.shape[axis_arr]
+    src = [slice(None)] * mask.ndim
+    dst = [slice(None)] * mask.ndim
+    if k > 0:
+        src[axis_arr] = slice(k, n)
+        dst[axis_arr] = slice(0, n - k)
+    else:
+        src[axis_arr] = slice(0, n + k)
+        dst[axis_arr] = slice(-k, n)
+    out[tuple(dst)] = mask[tuple(src)]
+    return out
+
+
+def laplacian_ib_nodes(mask, M):
+    """Interior nodes whose +-M/2 axial stencil reaches an in-array exterior node
+    (logical tuples, array order)."""
+    ext = ~mask
+    hit = np.zeros_like(mask)
+    d = mask.ndim
+    for a in range(d):
+        ax = d - 1 - a
+        for k in list(range(-(M // 2), 0)) + list(range(1, M // 2 + 1)):
+            hit |= _shifted(ext, ax, k)
+    return [tuple(int(v) for v in reversed(i)) for i in np.argwhere(mask & hit)]
+
+
+def scalar_bc_fn(bc, d):
+    return lambda Mp: taylor.bc_templates_scalar(bc, d, Mp)
+
+
+def vector_bc_fn(bc, d):
+    return lambda Mp: taylor.bc_templates_vector(bc, d, Mp)
+
+
+class Geometry:
+    """Discretised SDF with its interior masks and boundary points."""
+
+    def __init__(self, sdf, h, M):
+        self.sdf = np.asarray(sdf, dtype=np.float64)
+        self.h = float(h)
+        self.M = int(M)
+        self.sdf_g = self.sdf / self.h
+        self.mask = self.sdf_g > 0.0
+        self.lshape = logical_shape(self.sdf)
+        self.d = len(self.lshape)
+        self.bps = BoundaryPoints(self.sdf, self.h, self.M)
+
+    def vmask(self, a):
+        """Interior mask of the staggered v_a nodes (j + e_a/2): the mean of the
+        SDF at the two neighbouring nodes is > 0 (own value at the array end)."""
+        ax = self.d - 1 - a
+        s = self.sdf_g
+        n = s.shape[ax]
+        nb = np.array(s, copy=True)
+        sl_dst = [slice(None)] * s.ndim
+        sl_src = [slice(None)] * s.ndim
+        sl_dst[ax] = slice(0, n - 1)
+        sl_src[ax] = slice(1, n)
+        nb[tuple(sl_dst)] = s[tuple(sl_src)]
+        return 0.5 * (s + nb) > 0.0
+
+
+def laplacian_rows(geom, bc, opts, nodes=None):
+    """Modified-Laplacian corrections at IB nodes (grid units; divide by h^2).
+
+    Returns dict node -> (dict offset -> weight, info).
+    """
+    M = opts.M
+    w2 = [float(x) for x in taylor.central_second(M)]
+    H = M // 2
+    fields = [Field(geom.mask, np.zeros(geom.d), opts.eta_p)]
+    bcfn = scalar_bc_fn(bc, geom.d)
+    if nodes is None:
+        nodes = laplacian_ib_nodes(geom.mask, M)
+    out = {}
+    for node in nodes:
+        E = []
+        for a in range(geom.d):
+            for k in list(range(-H, 0)) + list(range(1, H + 1)):
+                nb = list(node)
+                nb[a] += k
+                if in_array(nb, geom.lshape) and not value(geom.mask, nb):
+                    E.append((0, np.array(nb, dtype=np.float64), w2[k + H]))
+        if not E:
+            continue
+        sup, c, info = fit(np.array(node, dtype=np.float64), fields, geom.bps, bcfn, E, opts, geom.lshape)
+        wts = {}
+        for (f, j), cj in zip(sup, c):
+            off = tuple(jj - nn for jj, nn in zip(j, node))
+            wts[off] = wts.get(off, 0.0) + float(cj)
+        out[node] = (wts, info)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# 1st-order staggered form
+# ---------------------------------------------------------------------------
+def gradient_ib_nodes(geom, a, M):
+    """Interior v_a nodes j whose forward-staggered d/dx_a stencil
+    (p at j + k e_a, k = -M/2+1 .. M/2) reaches an in-array exterior p node."""
+    vm = geom.vmask(a)
+    ext = ~geom.mask
+    ax = geom.d - 1 - a
+    hit = np.zeros_like(vm)
+    for k in range(-(M // 2) + 1, M // 2 + 1):
+        hit |= _shifted(ext, ax, k)
+    return [tuple(int(v) for v in reversed(i)) for i in np.argwhere(vm & hit)]
+
+
+def divergence_ib_nodes(geom, M):
+    """Interior p nodes whose backward-staggered divergence stencils
+    (v_a at j + k e_a, k = -M/2 .. M/2-1) reach an in-array exterior v node."""
+    hit = np.zeros_like(geom.mask)
+    for a in range(geom.d):
+        ext = ~geom.vmask(a)
+        ax = geom.d - 1 - a
+        for k in range(-(M // 2), M // 2):
+            hit |= _shifted(ext, ax, k)
+    return [tuple(int(v) for v in reversed(i)) for i in np.argwhere(geom.mask & hit)]
+
+
+def gradient_rows(geom, a, bc, opts, nodes=None):
+    """Corrections of the modified d/dx_a (grid units; divide by h) at v_a nodes.
+
+    Expansion point: the v_a node position j + e_a/2; fit on the pressure
+    field with the pressure BC hierarchy and eta_p.
+    Returns dict node j -> (dict p-offset -> weight, info).
+    """
+    M = opts.M
+    c = [float(x) for x in taylor.staggered_first(M)]      # at offsets -(M-1)/2..(M-1)/2
+    fields = [Field(geom.mask, np.zeros(geom.d), opts.eta_p)]
+    bcfn = scalar_bc_fn(bc, geom.d)
+    if nodes is None:
+        nodes = gradient_ib_nodes(geom, a, M)
+    ea = np.zeros(geom.d)
+    ea[a] = 0.5
+    out = {}
+    for node in nodes:
+        E = []
+        for k in range(-(M // 2) + 1, M // 2 + 1):
+            nb = list(node)
+            nb[a] += k
+            if in_array(nb, geom.lshape) and not value(geom.mask, nb):
+                E.append((0, np.array(nb, dtype=np.float64), c[k + M // 2 - 1]))
+        if not E:
+            continue
+        xi0 = np.array(node, dtype=np.float64) + ea
+        sup, cc, info = fit(xi0, fields, geom.bps, bcfn, E, opts, geom.lshape)
+        wts = {}
+        for (f, j), cj in zip(sup, cc):
+            off = tuple(jj - nn for jj, nn in zip(j, node))
+            wts[off] = wts.get(off, 0.0) + float(cj)
+        out[node] = (wts, info)
+    return out
+
+
+def divergence_rows(geom, bc, opts, nodes=None):
+    """Corrections of the modified divergence (grid units; divide by h) at p nodes.
+
+    Expansion point: the p node; coupled fit on all velocity components with
+    the velocity BC hierarchy and eta_v.
+    Returns dict node -> (dict (component, v-offset) -> weight, info).
+    """
+    M = opts.M
+    d = geom.d
+    c = [float(x) for x in taylor.staggered_first(M)]
+    fields = []
+    for a in range(d):
+        sh = np.zeros(d)
+        sh[a] = 0.5
+        fields.append(Field(geom.vmask(a), sh, opts.eta_v))
+    vmasks = [F.mask for F in fields]
+    bcfn = vector_bc_fn(bc, d)
+    if nodes is None:
+        nodes = divergence_ib_nodes(geom, M)
+    out = {}
+    for node in nodes:
+        E = []
+        for a in range(d):
+            for k in range(-(M // 2), M // 2):
+                nb = list(node)
+                nb[a] += k
+                if in_array(nb, geom.lshape) and not value(vmasks[a], nb):
+                    pos = np.array(nb, dtype=np.float64)
+                    pos[a] += 0.5
+                    E.append((a, pos, c[k + M // 2]))
+        if not E:
+            continue
+        sup, cc, info = fit(np.array(node, dtype=np.float64), fields, geom.bps, bcfn, E, opts, geom.lshape)
+        wts = {}
+        for (f, j), cj in zip(sup, cc):
+            off = (f,) + tuple(jj - nn for jj, nn in zip(j, node))
+            wts[off] = wts.get(off, 0.0) + float(cj)
+        out[node] = (wts, info)
+    return out

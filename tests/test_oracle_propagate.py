@@ -1,0 +1,193 @@
+"""Pins of the oracle's propagators: images, polarity, adjoint, stability (no GPU)."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import images, sim, stencils
+from paper_2309_03600_gb300 import inputs
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def _free_space_error(w, times, win):
+    """Same scheme, same source/receivers, no boundary: direct-wave error."""
+    sdf0 = np.full_like(w["sdf"], 1e6)
+    s0 = sim.Leapfrog(sdf0, w["vel"], w["h"], w["M"], "free", w["dt"], w["src"], w["rec"])
+    tr0 = s0.forward(w["wavelet"], w["nt"])
+    r = np.linalg.norm(w["rec"] - w["src"][0], axis=1)[:, None]
+    an0 = images.free_space_2d(images.ricker_fn(w["f0"]), r, times[None, :], w["c"])
+    return _rel(tr0[:, win], an0[:, win])
+
+
+@pytest.mark.parametrize("bc", ["free", "rigid"])
+def test_flat_surface_images_201(bc):
+    """201 x 201, h = 10 m, c = 1500 m/s, M = 4, C = 0.4, 500 steps, flat surface at
+    z = 40.3 h: traces match direct -/+ image within twice the free-space scheme
+    error over the window before the first edge reflection."""
+    w = inputs.workload_flat2d(bc=bc)
+    s = sim.Leapfrog(w["sdf"], w["vel"], w["h"], w["M"], bc, w["dt"], w["src"], w["rec"])
+    tr = s.forward(w["wavelet"], w["nt"])
+    times = (np.arange(w["nt"]) + 1) * w["dt"]
+    an = images.flat_surface_traces(images.ricker_fn(w["f0"]), w["src"][0], w["rec"], times,
+                                    w["c"], w["z0"], bc, 2)
+    win = times < 0.95
+    e_ib = _rel(tr[:, win], an[:, win])
+    e_free = _free_space_error(w, times, win)
+    assert e_ib <= 2.0 * e_free, (e_ib, e_free)
+    assert e_ib < 0.08
+
+
+def test_reflection_polarity():
+    """Free surface reflects with -1, rigid with +1: the reflected arrival at a
+    receiver has the sign of the image term."""
+    w = inputs.workload_flat2d()
+    times = (np.arange(w["nt"]) + 1) * w["dt"]
+    rec = np.array([[100 * w["h"], 60 * w["h"]]])
+    src = w["src"]
+    # reflected arrival time: image distance / c + wavelet delay
+    img = src[0].copy()
+    img[1] = 2 * w["z0"] - img[1]
+    t_ref = np.linalg.norm(rec[0] - img) / w["c"] + 1.5 / w["f0"]
+    t_dir = np.linalg.norm(rec[0] - src[0]) / w["c"] + 1.5 / w["f0"]
+    out = {}
+    for bc in ("free", "rigid"):
+        s = sim.Leapfrog(w["sdf"], w["vel"], w["h"], w["M"], bc, w["dt"], src, rec)
+        out[bc] = s.forward(w["wavelet"], w["nt"])[0]
+    diff = out["rigid"] - out["free"]          # = 2 x image term
+    k = int(round(t_ref / w["dt"])) - 1
+    kd = int(round(t_dir / w["dt"])) - 1
+    assert abs(diff[kd]) < 0.05 * abs(out["free"][kd])      # direct arrival unaffected
+    assert out["free"][k] * out["rigid"][k] < 0 or abs(diff[k]) > abs(out["free"][k])
+    sdf0 = np.full_like(w["sdf"], 1e6)
+    ref = sim.Leapfrog(sdf0, w["vel"], w["h"], w["M"], "free", w["dt"], src, rec).forward(
+        w["wavelet"], w["nt"])[0]
+    refl_free = out["free"][k] - ref[k]
+    refl_rigid = out["rigid"][k] - ref[k]
+    assert np.sign(refl_free) == -np.sign(refl_rigid)
+    # the reflected peak of a Ricker from a positive image term is positive
+    assert refl_rigid > 0 and refl_free < 0
+
+
+@pytest.mark.parametrize("bc", ["free", "rigid"])
+def test_tilted_line_images(bc):
+    """Tilted flat surface (17 degrees): direct -/+ image across the line."""
+    h, c, M = 10.0, 1500.0, 4
+    nx, nz = 201, 181
+    pt = np.array([1000.0, 503.0])
+    ang = 17.0
+    sdf = inputs.tilted_plane_sdf((nx, nz), h, pt, ang)
+    nrm = np.array([math.sin(math.radians(ang)), math.cos(math.radians(ang))])
+    dt = 0.4 * h / c
+    nt = 420
+    f0 = 10.0
+    src = np.array([[1000.0, 1100.0]])
+    rx = np.linspace(700.0, 1300.0, 31)
+    rec = np.stack([rx, 800.0 + (rx - 1000.0) * 0.0], axis=1)
+    vel = np.full((nz, nx), c)
+    s = sim.Leapfrog(sdf, vel, h, M, bc, dt, src, rec)
+    tr = s.forward(inputs.ricker(f0, dt, nt), nt)
+    times = (np.arange(nt) + 1) * dt
+    an = images.plane_traces(images.ricker_fn(f0), src[0], rec, times, c, pt, nrm, bc, 2)
+    win = times < 0.85
+    e_ib = _rel(tr[:, win], an[:, win])
+    s0 = sim.Leapfrog(np.full_like(sdf, 1e6), vel, h, M, bc, dt, src, rec)
+    tr0 = s0.forward(inputs.ricker(f0, dt, nt), nt)
+    r = np.linalg.norm(rec - src[0], axis=1)[:, None]
+    an0 = images.free_space_2d(images.ricker_fn(f0), r, times[None, :], c)
+    e_free = _rel(tr0[:, win], an0[:, win])
+    assert e_ib <= 2.0 * e_free, (e_ib, e_free)
+
+
+@pytest.mark.parametrize("bc", ["free", "rigid"])
+def test_staggered_flat_images(bc):
+    """First-order form, constant rho and c: p obeys p_tt = c^2 lap p + f_t, so
+    the traces are the images solution driven by the wavelet's derivative
+    (delayed by dt/2: the source sample n enters over [t_n, t_n+1])."""
+    h, c, M = 10.0, 1500.0, 4
+    nx, nz = 161, 161
+    z0 = 30.3 * h
+    sdf = inputs.flat_surface_sdf((nx, nz), h, z0)
+    dt = 0.3 * h / c
+    nt = 400
+    f0 = 10.0
+    src = np.array([[80 * h, 70 * h]])
+    rx = np.arange(50, 111, 2) * h
+    rec = np.stack([rx, np.full_like(rx, 36 * h)], axis=1)
+    vel = np.full((nz, nx), c)
+    rho = np.full((nz, nx), 1000.0)
+    s = sim.Staggered(sdf, vel, rho, h, M, bc, dt, src, rec)
+    tr = s.forward(inputs.ricker(f0, dt, nt), nt)
+    times = (np.arange(nt) + 1) * dt
+    dw = images.ricker_derivative_fn(f0, shift=0.5 * dt)
+    an = images.flat_surface_traces(dw, src[0], rec, times, c, z0, bc, 2)
+    win = times < 0.8
+    e = _rel(tr[:, win], an[:, win])
+    assert e < 0.05, e
+
+
+def _tiny_problem(bc="free"):
+    h, c, M = 10.0, 1500.0, 4
+    nx, nz = 36, 30
+    sdf = inputs.flat_surface_sdf((nx, nz), h, 6.35 * h)
+    rng = np.random.default_rng(9)
+    vel = c + 100.0 * rng.normal(size=(nz, nx))
+    dt = 0.35 * h / vel.max()
+    src = np.array([[17.3 * h, 20.6 * h]])
+    rec = np.array([[x * h, 9.5 * h] for x in range(8, 28, 3)])
+    s = sim.Leapfrog(sdf, vel, h, M, bc, dt, src, rec)
+    return s, vel, dt
+
+
+@pytest.mark.parametrize("bc", ["free", "rigid"])
+def test_adjoint_dot_product(bc):
+    """<F w, r> = <w, F^T r> for the wavelet -> traces map (exact adjoint)."""
+    s, vel, dt = _tiny_problem(bc)
+    nt = 90
+    rng = np.random.default_rng(1)
+    wv = rng.normal(size=nt)
+    r = rng.normal(size=(s.R.shape[0], nt))
+    tr, hist = s.forward(wv, nt, keep_history=True)
+    _, gw = s.adjoint(r, hist)
+    lhs = float(np.sum(tr * r))
+    rhs = float(np.dot(wv, gw))
+    assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + abs(rhs))
+
+
+@pytest.mark.parametrize("bc", ["free", "rigid"])
+def test_velocity_gradient_vs_finite_difference(bc):
+    s, vel, dt = _tiny_problem(bc)
+    nt = 90
+    wv = inputs.ricker(25.0, dt, nt)
+    rng = np.random.default_rng(2)
+    dobs = s.with_velocity(vel * 1.01).forward(wv, nt)
+
+    def J(v):
+        tr = s.with_velocity(v).forward(wv, nt)
+        return 0.5 * float(np.sum((tr - dobs) ** 2)), tr
+
+    J0, tr0 = J(vel)
+    _, hist = s.forward(wv, nt, keep_history=True)
+    g, _ = s.adjoint(tr0 - dobs, hist)
+    dv = rng.normal(size=vel.shape) * s.geom.mask
+    eps = 1e-3
+    fd = (J(vel + eps * dv)[0] - J(vel - eps * dv)[0]) / (2 * eps)
+    an = float(np.dot(g, dv.ravel()))
+    assert abs(fd - an) <= 1e-6 * abs(fd), (fd, an)
+
+
+def test_bounded_long_run_order8_defaults():
+    """Order-8 interior with the default extrapolation basis: 3000 source-free
+    steps after injection on a seeded sinusoidal surface stay bounded."""
+    ws = inputs.workload_sinusoid_staggered(nx=121, nz=101, h=5.0, M=8, nt=300)
+    src = np.array([[300.0, 350.0]])
+    s = sim.Leapfrog(ws["sdf"], ws["vel"], 5.0, 8, "free", ws["dt"], src, ws["rec"][:40])
+    nt = 3000
+    wl = np.zeros(nt)
+    wl[:300] = ws["wavelet"]
+    tr = s.forward(wl, nt)
+    early = np.abs(tr[:, :1000]).max()
+    late = np.abs(tr[:, 2000:]).max()
+    assert late < 2.0 * early, (early, late)
