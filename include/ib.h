@@ -1,0 +1,222 @@
+/*
+ * ib.h -- C ABI of the GB300 immersed-boundary acoustic finite-difference library.
+ *
+ * Method (Caunt, Nelson, Luporini, Gorman, "A Novel Immersed Boundary Approach
+ * for Irregular Topography with Acoustic Wave Equations"): grid points near an
+ * irregular surface, given as a signed-distance field (SDF) discretised on the
+ * FD grid, get modified derivative stencils.  Exterior values needed by an
+ * interior stencil are extrapolated by an N-dimensional truncated Taylor
+ * polynomial fitted, by the Moore-Penrose pseudoinverse, to interior values
+ * and to boundary conditions imposed at boundary points inside a
+ * hyperspherical support ("Approximating Boundary Conditions",
+ * "Reconciliation with the Interior Numerical Discretization").  The modified
+ * operators drive explicit time stepping of the second-order acoustic wave
+ * equation (2nd-order application section) or of the first-order staggered
+ * pressure-velocity system (1st-order section).
+ *
+ * Conventions shared by every entry point
+ *   - Grid: ndim = 2 or 3, n[0] = nx (fastest), n[1] = nz (2D) or ny (3D),
+ *     n[2] = nz (3D); arrays are row-major [nz][nx] or [nz][ny][nx].  Node
+ *     (i_x, .., i_z) sits at (i_x h, .., i_z h); z is depth (positive down).
+ *   - SDF s > 0 in the physical domain; a node with s <= 0 is exterior and its
+ *     fields are held at zero.  Values beyond the array are zero (zero
+ *     Dirichlet edges, as in the paper's examples).
+ *   - Coordinates (sources, receivers) are metres in logical order
+ *     (x, [y,] z), float64, in DEVICE memory.
+ *   - Every array argument named *_dev is a device pointer; the caller owns
+ *     it.  The library owns tables and its internal scratch (wavefields).
+ *   - Work is enqueued on `stream` (a cudaStream_t, NULL = legacy default
+ *     stream).  Entry points return after enqueueing; argument errors are
+ *     returned synchronously; device-side faults surface from the next call
+ *     or from ib_sync_status().
+ *   - No entry point throws.  On failure the status is non-zero and
+ *     ib_last_error() returns a thread-local message.
+ *   - A table may be used concurrently by several streams for forward and
+ *     adjoint runs (read-only); building or freeing it must not overlap them.
+ */
+#ifndef IB_H
+#define IB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    IB_OK = 0,
+    IB_ERR_ARG = 1,       /* invalid argument (shape, order, pointer, size)        */
+    IB_ERR_RANK = 2,      /* a node stayed unconstrained at the largest radius
+                             and the lowest basis order (rank paragraph)           */
+    IB_ERR_CUDA = 3,      /* a CUDA call failed                                    */
+    IB_ERR_OOM = 4,       /* device allocation failed                              */
+    IB_ERR_UNSTABLE = 5,  /* NaN/Inf detected in the wavefield                     */
+    IB_ERR_TIMEOUT = 6,   /* a bounded device wait gave up                         */
+    IB_ERR_STATE = 7      /* call not valid for this table (e.g. wrong form)       */
+} ib_status;
+
+typedef enum { IB_FREE = 0, IB_RIGID = 1 } ib_bc;
+typedef enum { IB_SECOND_ORDER = 0, IB_FIRST_ORDER_STAGGERED = 1 } ib_form;
+
+typedef struct {
+    int32_t ndim;          /* 2 or 3                                               */
+    int32_t reserved;
+    int64_t n[3];          /* nx, (ny,) nz; unused entries 1                       */
+    double h;              /* grid step (metres), isotropic                        */
+} ib_grid;
+
+typedef struct {
+    int32_t space_order;   /* M of the interior stencils: 2, 4, 6 or 8             */
+    int32_t basis_order;   /* order of the extrapolation basis; 0 -> min(M, 4)     */
+    int32_t min_order;     /* lowest basis order of the fallback (>= 2)            */
+    int32_t reserved;
+    double radius;         /* initial support radius in grid units; <= 0 ->
+                              (basis_order + 1) / 2 (support paragraph)            */
+    double growth;         /* radius grows by 0.5 up to radius + growth            */
+    double eta_p;          /* pressure cut-off eta (paper: 0.5)                    */
+    double eta_v;          /* velocity cut-off eta (paper: 0)                      */
+    double rank_tol;       /* full rank iff sigma_min > rank_tol * sigma_max       */
+} ib_opts;
+
+/* Fill `opts` with the defaults for space order M (basis min(M,4), min order
+ * 2, radius (basis+1)/2, growth 3, eta_p 0.5, eta_v 0, rank_tol 1e-10). */
+void ib_opts_default(ib_opts* opts, int32_t space_order);
+
+typedef struct ib_table ib_table;   /* opaque, library-owned */
+
+/*
+ * ib_build_stencils -- geometry, boundary points and modified stencils.
+ * Paper: boundary points and eta cut-off (boundary-point paragraph of
+ * "Approximating Boundary Conditions"); support growth and rank test (rank
+ * paragraph); fit by pseudoinverse and extrapolation B A^+ ("Reconciliation
+ * ..."); free-surface and velocity free-surface hierarchies.
+ *   grid     host pointer, read during the call.
+ *   sdf_dev  device float64 [N] SDF in metres (N = nx*ny*nz), read during the
+ *            call (the call synchronises `stream` before returning).
+ *   bc       IB_FREE or IB_RIGID;  form: IB_SECOND_ORDER (modified Laplacian)
+ *            or IB_FIRST_ORDER_STAGGERED (modified gradients at velocity
+ *            nodes and modified divergence at pressure nodes).
+ *   opts     host pointer or NULL (defaults for M = 4).
+ *   out      receives a new table; free with ib_table_free.
+ * Errors: IB_ERR_ARG (shape/order), IB_ERR_RANK (some node could not be
+ * constrained; the table is still returned with those rows marked and left
+ * unmodified beyond the standard stencil), IB_ERR_OOM, IB_ERR_CUDA.
+ */
+ib_status ib_build_stencils(const ib_grid* grid, const double* sdf_dev, ib_bc bc,
+                            ib_form form, const ib_opts* opts, ib_table** out,
+                            void* stream);
+
+void ib_table_free(ib_table* table);
+
+/* Per-operator statistics of a table. */
+typedef struct {
+    int32_t n_ops;              /* 1 (Laplacian) or 2*ndim (staggered: the ndim
+                                   gradients at velocity nodes, then the divergence
+                                   blocks, one per velocity component)              */
+    int32_t ndim;
+    int64_t rows[8];            /* IB rows per operator                              */
+    int64_t nnz[8];             /* correction entries per operator                   */
+    int64_t n_boundary_points;  /* accepted boundary points                          */
+    int64_t n_rank_failures;    /* rows left without a correction                    */
+    int64_t n_grown;            /* rows whose support grew beyond the first radius   */
+    int64_t n_reduced;          /* rows whose basis order was lowered                */
+    int64_t table_bytes;        /* device bytes of the correction tables             */
+    double setup_seconds;       /* wall time of ib_build_stencils                    */
+} ib_table_info;
+
+ib_status ib_table_stats(const ib_table* table, ib_table_info* info);
+
+/*
+ * ib_table_export -- copy one operator's corrections to HOST buffers (for
+ * inspection and tests).  op indexes as in ib_table_info.  Columns are given as
+ * integer node offsets (dx, dy, dz) from the row node (x_row, y_row, z_row).
+ *   row_node   int64 [rows]   linear index of the row node in [nz][ny][nx]
+ *   row_ptr    int64 [rows+1]
+ *   col_off    int32 [nnz][3] (dx, dy, dz); dy = 0 in 2D
+ *   weight     float64 [nnz]  correction weight in grid units (multiply by
+ *                             1/h^2 for the Laplacian, 1/h for first derivatives)
+ *   row_info   int32 [rows][4] (radius in half grid units, basis order,
+ *                             boundary points used, status 0 ok / 1 rank failure)
+ * Any pointer may be NULL to skip it.  Buffers must hold the sizes reported
+ * by ib_table_stats.
+ */
+ib_status ib_table_export(const ib_table* table, int32_t op, int64_t* row_node,
+                          int64_t* row_ptr, int32_t* col_off, double* weight,
+                          int32_t* row_info);
+
+/*
+ * One shot: model, sources, receivers.  Element type of vel/rho/wavelet/
+ * traces is float for precision 32 and double for precision 64.
+ */
+typedef struct {
+    const void* vel_dev;        /* [N] wave speed c (m/s)                            */
+    const void* rho_dev;        /* [N] density (kg/m^3) or NULL = 1; first-order form */
+    const double* src_dev;      /* [nsrc][ndim] metres                               */
+    const double* rec_dev;      /* [nrec][ndim] metres                               */
+    const void* wavelet_dev;    /* [nt] source time function, sample n is used in
+                                   the step that produces p^{n+1}                    */
+    void* traces_dev;           /* [nrec][nt] output: trace[r][n] = p^{n+1} at r     */
+    int32_t nsrc;
+    int32_t nrec;
+} ib_shot;
+
+/*
+ * ib_forward -- nt explicit time steps (2nd-order application section:
+ *   p^{n+1} = 2p^n - p^{n-1} + dt^2 c^2 L_mod p^n + dt^2 f^n;
+ * 1st-order section: v += dt/rho G_mod p;  p += dt rho c^2 D_mod v + dt f),
+ * p^0 = p^{-1} = 0, fused source injection (multilinear delta, 1/h^d) and
+ * receiver interpolation (multilinear, exterior nodes read as zero).
+ *   precision  32 or 64.
+ *   dt         time step (s); nt >= 1.
+ *   ckpt_dev   NULL, or device buffer of ib_checkpoint_bytes(table, precision,
+ *              nt, n_ckpt) bytes that receives the wavefield checkpoints the
+ *              adjoint needs (second-order form only); n_ckpt >= 1.
+ * Errors: IB_ERR_ARG, IB_ERR_STATE, IB_ERR_OOM, IB_ERR_CUDA.
+ */
+ib_status ib_forward(const ib_table* table, const ib_shot* shot, int32_t precision,
+                     double dt, int32_t nt, void* ckpt_dev, int32_t n_ckpt, void* stream);
+
+/* Bytes of the checkpoint buffer for (precision, nt, n_ckpt). */
+int64_t ib_checkpoint_bytes(const ib_table* table, int32_t precision, int32_t nt,
+                            int32_t n_ckpt);
+
+/*
+ * ib_adjoint -- exact transpose of the discrete second-order map (the
+ * modified operator transposed, source and receiver maps transposed) with
+ * checkpointed recomputation of the forward wavefield.  For
+ * J = 1/2 sum_{r,n} (trace[r][n] - d[r][n])^2 and residual = trace - d:
+ *   grad_vel_dev[x]     = dJ/dc(x)  (zero at exterior nodes), overwritten;
+ *   grad_wavelet_dev[n] = dJ/dw[n]  if not NULL, overwritten.
+ * The shot, dt, nt, precision and n_ckpt must be those of the ib_forward call
+ * that filled ckpt_dev.  The shot's traces_dev is not read.
+ */
+ib_status ib_adjoint(const ib_table* table, const ib_shot* shot, int32_t precision,
+                     double dt, int32_t nt, const void* ckpt_dev, int32_t n_ckpt,
+                     const void* residual_dev, void* grad_vel_dev,
+                     void* grad_wavelet_dev, void* stream);
+
+/*
+ * ib_forward_batch -- many independent shots, each with its own table (grid
+ * and topography), advanced together: every time step is one launch that
+ * covers the tiles of all shots.  Same semantics per shot as ib_forward
+ * (precision 32, no checkpoints).  tables[i] and shots[i] are host arrays of
+ * length nshot.
+ */
+ib_status ib_forward_batch(const ib_table* const* tables, const ib_shot* shots,
+                           int32_t nshot, int32_t precision, double dt, int32_t nt,
+                           void* stream);
+
+/* Synchronise `stream` and return IB_ERR_CUDA on a pending device error. */
+ib_status ib_sync_status(void* stream);
+
+/* Thread-local message of the last failure ("" if none). */
+const char* ib_last_error(void);
+
+/* Library version string. */
+const char* ib_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* IB_H */

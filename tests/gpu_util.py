@@ -1,0 +1,66 @@
+"""Helpers shared by the GPU parity tests (comparison of library tables and
+traces with the oracle)."""
+import numpy as np
+import torch
+
+from oracle import sim, stencils
+
+
+def lin_to_node(lin, shape):
+    """Array-order linear index -> logical node (x, [y,] z)."""
+    idx = np.unravel_index(int(lin), shape)
+    return tuple(int(v) for v in reversed(idx))
+
+
+def gpu_rows(exp, shape, comp_prefix=None):
+    """Table export -> {node: ({offset: w}, info)} with offsets in logical order."""
+    ndim = len(shape)
+    out = {}
+    for r, lin in enumerate(exp["row_node"]):
+        node = lin_to_node(lin, shape)
+        ent = {}
+        for k in range(exp["row_ptr"][r], exp["row_ptr"][r + 1]):
+            c = exp["col"][k]
+            off = (int(c[0]), int(c[2])) if ndim == 2 else (int(c[0]), int(c[1]), int(c[2]))
+            if comp_prefix is not None:
+                off = (comp_prefix,) + off
+            ent[off] = float(exp["w"][k])
+        out[node] = (ent, tuple(int(v) for v in exp["info"][r]))
+    return out
+
+
+def compare_tables(orc, gpu, rtol=1e-8, check_info=True):
+    """Same IB nodes, same support sets, weights equal to rtol * max|w| of the row.
+    Returns the largest relative difference seen."""
+    assert set(orc) == set(gpu), (sorted(set(orc) ^ set(gpu))[:10], len(orc), len(gpu))
+    worst = 0.0
+    for node, (wo, info) in orc.items():
+        wg, ginfo = gpu[node]
+        assert ginfo[3] == 0, (node, ginfo)
+        if check_info:
+            assert ginfo[0] == int(round(2 * info["radius"])), (node, ginfo, info["radius"])
+            assert ginfo[1] == info["order"], (node, ginfo, info["order"])
+        assert set(wo) == set(wg), (node, sorted(set(wo) ^ set(wg)))
+        if not wo:
+            continue
+        scale = max(1e-300, max(abs(v) for v in wo.values()))
+        d = max(abs(wo[k] - wg[k]) for k in wo) / scale
+        worst = max(worst, d)
+        assert d <= rtol, (node, d)
+    return worst
+
+
+def split_div(orc_div, comp):
+    """Oracle divergence rows -> rows of one velocity component."""
+    out = {}
+    for node, (w, info) in orc_div.items():
+        out[node] = ({k: v for k, v in w.items() if k[0] == comp}, info)
+    return out
+
+
+def cuda(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=dtype, device="cuda")
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))

@@ -1,0 +1,272 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 oracle."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import sim, stencils
+from paper_2309_03600_gb300 import inputs
+from gpu_util import compare_tables, cuda, gpu_rows, rel_l2, split_div
+
+pytestmark = pytest.mark.gpu
+
+ib = pytest.importorskip("paper_2309_03600_gb300.ib")
+
+
+def circle_sdf(nx, nz, cx, cz, R, h=1.0):
+    x = np.arange(nx)[None, :] - cx
+    z = np.arange(nz)[:, None] - cz
+    return (np.sqrt(x * x + z * z) - R) * h
+
+
+def small_hills(nx=40, ny=36, nz=34, h=10.0, seed=13):
+    prm = inputs.hills_params(5, seed, (nx - 1) * h, (ny - 1) * h, hmin=20, hmax=90, smin=60, smax=160)
+    parts = inputs.hills_surface(prm, datum=160.0, zmin=30.0)
+    sdf, zs = inputs.heightfield_sdf_3d(nx, ny, nz, h, parts)
+    return sdf, zs
+
+
+# ---------------------------------------------------------------------------
+# stencil tables
+# ---------------------------------------------------------------------------
+def _lap_case(sdf, h, M, bc, **kw):
+    geom = stencils.Geometry(sdf, h, M)
+    opts = stencils.Opts(M, **kw)
+    orc = stencils.laplacian_rows(geom, bc, opts)
+    o = ib.ib_opts_default(M)
+    if "ib_order" in kw:
+        o.basis_order = kw["ib_order"]
+    t = ib.ib_build_stencils(cuda(sdf), h, bc, "second", M, opts=o)
+    gpu = gpu_rows(t.export(0), sdf.shape)
+    return orc, gpu, t
+
+
+@pytest.mark.parametrize("bc", ["free", "rigid"])
+@pytest.mark.parametrize("M", [2, 4, 8])
+def test_table_flat2d(bc, M):
+    sdf = inputs.flat_surface_sdf((48, 40), 10.0, 12.3 * 10.0)
+    orc, gpu, t = _lap_case(sdf, 10.0, M, bc)
+    assert len(orc) > 0
+    compare_tables(orc, gpu, rtol=1e-9)
+    st = t.stats()
+    assert st["n_rank_failures"] == 0
+    assert st["n_boundary_points"] == 48
+
+
+@pytest.mark.parametrize("bc", ["free", "rigid"])
+def test_table_circle2d(bc):
+    sdf = circle_sdf(56, 52, 27.3, 25.6, 13.7, h=5.0)
+    orc, gpu, _ = _lap_case(sdf, 5.0, 8, bc)
+    compare_tables(orc, gpu, rtol=1e-8)
+
+
+@pytest.mark.parametrize("bc", ["free", "rigid"])
+def test_table_sinusoid2d_order8(bc):
+    w = inputs.workload_sinusoid_staggered(nx=161, nz=101, h=5.0, M=8, nt=10)
+    orc, gpu, _ = _lap_case(w["sdf"], 5.0, 8, bc)
+    compare_tables(orc, gpu, rtol=1e-8)
+
+
+def test_table_sinusoid2d_basis8():
+    """Full order-8 basis (45 unknowns) on the GPU constructor."""
+    w = inputs.workload_sinusoid_staggered(nx=121, nz=81, h=5.0, M=8, nt=10)
+    orc, gpu, _ = _lap_case(w["sdf"], 5.0, 8, "free", ib_order=8)
+    compare_tables(orc, gpu, rtol=1e-7)
+
+
+@pytest.mark.parametrize("M", [4, 8])
+def test_table_hills3d(M):
+    sdf, _ = small_hills()
+    orc, gpu, _ = _lap_case(sdf, 10.0, M, "free")
+    assert len(orc) > 300
+    compare_tables(orc, gpu, rtol=1e-8)
+
+
+@pytest.mark.parametrize("bc", ["free", "rigid"])
+@pytest.mark.parametrize("M", [4, 8])
+def test_table_staggered2d(bc, M):
+    w = inputs.workload_sinusoid_staggered(nx=121, nz=81, h=5.0, M=M, nt=10)
+    geom = stencils.Geometry(w["sdf"], 5.0, M)
+    opts = stencils.Opts(M)
+    t = ib.ib_build_stencils(cuda(w["sdf"]), 5.0, bc, "staggered", M)
+    st = t.stats()
+    assert st["n_ops"] == 4
+    for a in range(2):
+        orc = stencils.gradient_rows(geom, a, bc, opts)
+        compare_tables(orc, gpu_rows(t.export(a), w["sdf"].shape), rtol=1e-8)
+    orc_div = stencils.divergence_rows(geom, bc, opts)
+    for a in range(2):
+        compare_tables(split_div(orc_div, a), gpu_rows(t.export(2 + a), w["sdf"].shape, comp_prefix=a),
+                       rtol=1e-7)
+
+
+# ---------------------------------------------------------------------------
+# propagation
+# ---------------------------------------------------------------------------
+def _run_leap(w, bc, dtype, nt=None):
+    nt = nt or w["nt"]
+    t = ib.ib_build_stencils(cuda(w["sdf"]), w["h"], bc, "second", w["M"])
+    tr = ib.ib_forward(t, cuda(w["vel"], dtype), cuda(w["wavelet"][:nt], dtype), cuda(w["src"]), cuda(w["rec"]),
+                       w["dt"], nt)
+    ib.ib_sync_status()
+    return tr.double().cpu().numpy()
+
+
+def _oracle_leap(w, bc, nt=None):
+    nt = nt or w["nt"]
+    s = sim.Leapfrog(w["sdf"], w["vel"], w["h"], w["M"], bc, w["dt"], w["src"], w["rec"])
+    return s.forward(w["wavelet"][:nt], nt)
+
+
+@pytest.mark.parametrize("bc", ["free", "rigid"])
+def test_forward_flat2d_201(bc):
+    """201 x 201, M = 4, 500 steps, flat surface at z = 40.3 h: FP64 traces to
+    1e-10 and FP32 traces to 1e-5 relative L2 against the FP64 oracle."""
+    w = inputs.workload_flat2d(bc=bc)
+    ref = _oracle_leap(w, bc)
+    e64 = rel_l2(_run_leap(w, bc, torch.float64), ref)
+    e32 = rel_l2(_run_leap(w, bc, torch.float32), ref)
+    assert e64 < 1e-10, e64
+    assert e32 < 1e-5, e32
+
+
+@pytest.mark.parametrize("bc", ["free", "rigid"])
+def test_forward_sinusoid2d_order8(bc):
+    w = inputs.workload_sinusoid_staggered(nx=161, nz=121, h=5.0, M=8, nt=800)
+    w["src"] = np.array([[400.0, 350.0]])
+    w["rec"] = w["rec"][:60]
+    w["vel"] = w["vel"].astype(np.float64)
+    ref = _oracle_leap(w, bc)
+    e64 = rel_l2(_run_leap(w, bc, torch.float64), ref)
+    e32 = rel_l2(_run_leap(w, bc, torch.float32), ref)
+    assert e64 < 1e-10, e64
+    assert e32 < 1e-5, e32
+
+
+@pytest.mark.parametrize("M", [4, 8])
+def test_forward_hills3d(M):
+    sdf, zs = small_hills()
+    h = 10.0
+    nx, ny, nz = 40, 36, 34
+    vel = np.full(sdf.shape, 1800.0)
+    dt = 0.4 * h / 1800.0
+    nt = 160
+    src = np.array([[20 * h, 17 * h, 26 * h]])
+    rec = np.array([[x * h, y * h, zs[y, x] + 2 * h] for x in range(4, 36, 5) for y in range(4, 32, 5)])
+    w = dict(sdf=sdf, vel=vel, h=h, M=M, dt=dt, nt=nt, src=src, rec=rec, wavelet=inputs.ricker(25.0, dt, nt))
+    ref = _oracle_leap(w, "free")
+    e32 = rel_l2(_run_leap(w, "free", torch.float32), ref)
+    e64 = rel_l2(_run_leap(w, "free", torch.float64), ref)
+    assert e64 < 1e-10, e64
+    assert e32 < 1e-5, e32
+
+
+@pytest.mark.parametrize("bc", ["free", "rigid"])
+@pytest.mark.parametrize("M", [4, 8])
+def test_forward_staggered2d(bc, M):
+    w = inputs.workload_sinusoid_staggered(nx=161, nz=121, h=5.0, M=M, nt=600)
+    w["src"] = np.array([[400.0, 350.0]])
+    w["rec"] = w["rec"][:60]
+    s = sim.Staggered(w["sdf"], w["vel"], w["rho"], 5.0, M, bc, w["dt"], w["src"], w["rec"])
+    ref = s.forward(w["wavelet"], w["nt"])
+    t = ib.ib_build_stencils(cuda(w["sdf"]), 5.0, bc, "staggered", M)
+    out = {}
+    for dt_ in (torch.float64, torch.float32):
+        tr = ib.ib_forward(t, cuda(w["vel"], dt_), cuda(w["wavelet"], dt_), cuda(w["src"]), cuda(w["rec"]),
+                           w["dt"], w["nt"], rho=cuda(w["rho"], dt_))
+        out[dt_] = tr.double().cpu().numpy()
+    e64 = rel_l2(out[torch.float64], ref)
+    e32 = rel_l2(out[torch.float32], ref)
+    assert e64 < 1e-10, e64
+    assert e32 < 1e-5, e32
+
+
+# ---------------------------------------------------------------------------
+# adjoint
+# ---------------------------------------------------------------------------
+def _tiny(bc):
+    h, c, M = 10.0, 1500.0, 4
+    nx, nz = 36, 30
+    sdf = inputs.flat_surface_sdf((nx, nz), h, 6.35 * h)
+    rng = np.random.default_rng(9)
+    vel = c + 100.0 * rng.normal(size=(nz, nx))
+    dt = 0.35 * h / vel.max()
+    src = np.array([[17.3 * h, 20.6 * h]])
+    rec = np.array([[x * h, 9.5 * h] for x in range(8, 28, 3)])
+    return sdf, vel, h, M, dt, src, rec
+
+
+@pytest.mark.parametrize("bc", ["free", "rigid"])
+@pytest.mark.parametrize("n_ckpt", [1, 7])
+def test_adjoint_vs_oracle(bc, n_ckpt):
+    sdf, vel, h, M, dt, src, rec = _tiny(bc)
+    nt = 90
+    rng = np.random.default_rng(4)
+    wv = inputs.ricker(25.0, dt, nt)
+    res = rng.normal(size=(rec.shape[0], nt))
+    s = sim.Leapfrog(sdf, vel, h, M, bc, dt, src, rec)
+    _, hist = s.forward(wv, nt, keep_history=True)
+    g_ref, gw_ref = s.adjoint(res, hist)
+    t = ib.ib_build_stencils(cuda(sdf), h, bc, "second", M)
+    v = cuda(vel)
+    nb = ib.ib_checkpoint_bytes(t, 64, nt, n_ckpt)
+    ck = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+    ib.ib_forward(t, v, cuda(wv), cuda(src), cuda(rec), dt, nt, ckpt=ck, n_ckpt=n_ckpt)
+    g, gw = ib.ib_adjoint(t, v, cuda(wv), cuda(src), cuda(rec), dt, nt, ck, n_ckpt, cuda(res),
+                          want_wavelet_grad=True)
+    ib.ib_sync_status()
+    assert rel_l2(g.cpu().numpy().ravel(), g_ref) < 1e-10
+    assert rel_l2(gw.cpu().numpy(), gw_ref) < 1e-10
+
+
+def test_adjoint_dot_product_fp32():
+    """<F w, r> = <w, F^T r> through the library in FP32."""
+    w = inputs.workload_flat2d(nx=121, nz=101, nt=300, z0_cells=20.3, src_cells=(60.0, 55.0),
+                               rec_x_cells=(30, 90), rec_z_cells=24)
+    t = ib.ib_build_stencils(cuda(w["sdf"]), w["h"], "free", "second", w["M"])
+    rng = np.random.default_rng(3)
+    nt = w["nt"]
+    wv = cuda(rng.normal(size=nt), torch.float32)
+    r = cuda(rng.normal(size=(w["rec"].shape[0], nt)), torch.float32)
+    v = cuda(w["vel"], torch.float32)
+    nb = ib.ib_checkpoint_bytes(t, 32, nt, 10)
+    ck = torch.zeros(nb, dtype=torch.uint8, device="cuda")
+    tr = ib.ib_forward(t, v, wv, cuda(w["src"]), cuda(w["rec"]), w["dt"], nt, ckpt=ck, n_ckpt=10)
+    _, gw = ib.ib_adjoint(t, v, wv, cuda(w["src"]), cuda(w["rec"]), w["dt"], nt, ck, 10, r,
+                          want_wavelet_grad=True)
+    lhs = float((tr.double() * r.double()).sum())
+    rhs = float((wv.double() * gw.double()).sum())
+    assert abs(lhs - rhs) <= 1e-4 * (abs(lhs) + abs(rhs)), (lhs, rhs)
+
+
+def test_autograd_function():
+    sdf, vel, h, M, dt, src, rec = _tiny("free")
+    nt = 60
+    wv = inputs.ricker(25.0, dt, nt)
+    t = ib.ib_build_stencils(cuda(sdf), h, "free", "second", M)
+    v = cuda(vel).requires_grad_(True)
+    tr = ib.Forward.apply(v, t, cuda(wv), cuda(src), cuda(rec), dt, nt, 5)
+    loss = 0.5 * (tr ** 2).sum()
+    loss.backward()
+    s = sim.Leapfrog(sdf, vel, h, M, "free", dt, src, rec)
+    ref_tr, hist = s.forward(wv, nt, keep_history=True)
+    g_ref, _ = s.adjoint(ref_tr, hist)
+    assert rel_l2(v.grad.detach().cpu().numpy().ravel(), g_ref) < 1e-10
+
+
+# ---------------------------------------------------------------------------
+# errors
+# ---------------------------------------------------------------------------
+def test_argument_errors():
+    sdf = cuda(inputs.flat_surface_sdf((20, 20), 1.0, 5.3))
+    with pytest.raises(ib.IbError) as e:
+        ib.ib_build_stencils(sdf, 1.0, "free", "second", 5)
+    assert e.value.status == ib.IB_ERR_ARG
+    with pytest.raises(ib.IbError) as e:
+        ib.ib_build_stencils(sdf, -1.0, "free", "second", 4)
+    assert e.value.status == ib.IB_ERR_ARG
+    t = ib.ib_build_stencils(sdf, 1.0, "free", "second", 4)
+    v = cuda(np.ones((20, 20)))
+    with pytest.raises(ib.IbError):
+        ib.ib_forward(t, v, cuda(np.zeros(5)), cuda(np.zeros((1, 2))), cuda(np.zeros((1, 2))), -1.0, 5)
