@@ -1,0 +1,423 @@
+#!/usr/bin/env python
+"""Benchmark: grid-point updates/s of the immersed-boundary wave propagator.
+
+One step = one whole shot through the C ABI: ib_build_stencils (boundary
+points, IB rows, constrained FP64 fits, packing) + ib_forward over all time
+steps (fused stencil + IB gather, source injection, receiver interpolation).
+The default workload is the 2D first-order staggered pressure-velocity case:
+1001 x 1001 nodes, h = 5 m, space order 8, FP32, 3000 time steps, free surface
+z_s(x) = 200 + 60 sin(2 pi x / 1500) m, four seeded layers, 12 Hz Ricker, 500
+receivers 10 m below the surface (synthetic inputs; the paper's DEM is not
+available).
+
+Prints one JSON line (see the keys below).  --impl reference times the FP64
+CPU oracle on a bounded crop of the same workload instead.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "grid-pt updates/s vs HBM roofline (plain vs batched/adjoint); IB setup pts/s"
+UNIT = "grid-pt updates/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="stag2d", choices=["stag2d", "hills3d", "flat2d"])
+    ap.add_argument("--bc", default="free", choices=["free", "rigid"])
+    ap.add_argument("--nt", type=int, default=0, help="override time steps (testing only)")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# workloads
+# ---------------------------------------------------------------------------
+def make_workload(name, bc, rank=0, nt=0):
+    from paper_2309_03600_gb300 import inputs
+    if name == "stag2d":
+        w = inputs.workload_sinusoid_staggered(bc=bc, seed=2 + 1000 * rank)
+        w["form"] = "staggered"
+        w["desc"] = ("2D first-order staggered p-v, 1001x1001, h=5 m, order 8, FP32, 3000 steps, "
+                     "sinusoid %s surface, 4 layers, 12 Hz Ricker, 500 receivers" % bc)
+    elif name == "hills3d":
+        w = inputs.workload_hills3d(bc=bc, seed=3 + 1000 * rank, device="cuda")
+        w["form"] = "second"
+        w["rho"] = None
+        w["desc"] = ("3D second-order, 512x512x384, h=10 m, order 8, FP32, 2000 steps at CFL 0.45, "
+                     "12 Gaussian hills %s surface, smooth random velocity, 256x256 receivers" % bc)
+    else:
+        w = inputs.workload_flat2d(bc=bc)
+        w["form"] = "second"
+        w["rho"] = None
+        w["desc"] = "2D second-order, 201x201, h=10 m, order 4, FP64, 500 steps, flat %s surface z=40.3h" % bc
+    if nt:
+        w["nt"] = nt
+        w["wavelet"] = w["wavelet"][:nt]
+    w["dtype"] = "f64" if name == "flat2d" else "f32"
+    return w
+
+
+def grid_points(w):
+    n = 1
+    for v in w["shape"]:
+        n *= v
+    return n
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.rows = []
+        self.proc = None
+        self.idx = gpu_index
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "--query-gpu=" + self.Q, "--format=csv,noheader,nounits",
+                                          "-i", str(self.idx), "-lms", "200"], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for n, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(n)
+            except Exception:
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# roofline bookkeeping
+# ---------------------------------------------------------------------------
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_bytes(w, stats, precision_bytes=4):
+    """Algorithmic DRAM bytes of one launch of each time-step kernel: every
+    array the kernel must touch read or written once, plus its correction
+    tables (weight + column offset per entry, row index/pointer/tile-order per
+    row) and one field value per correction entry."""
+    N = grid_points(w)
+    e = precision_bytes
+    rows, nnz = stats["rows"], stats["nnz"]
+
+    def ib(ops):
+        return sum(nnz[o] * (e + 8 + e) + rows[o] * (8 + 8 + 4) for o in ops)
+
+    if w["form"] == "staggered":
+        # v: read p, vx, vz, bx, bz; write vx, vz.   p: read vx, vz, p, kp; write p.
+        return {"stag_v2d_f32": 7 * e * N + ib([0, 1]), "stag_p2d_f32": 5 * e * N + ib([2, 3])}
+    name = "leap%dd_%s" % (len(w["shape"]), "f64" if e == 8 else "f32")
+    # read p, p_prev, K; write p_next
+    return {name: 4 * e * N + ib([0])}
+
+
+def dram_traffic(kernel):
+    """Per-launch DRAM bytes from a committed ncu summary, if it is current."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        ent = d.get(kernel)
+        if not ent:
+            return None
+        import hashlib
+        h = hashlib.sha256()
+        for f in sorted(ent.get("sources", [])):
+            h.update(open(os.path.join(ROOT, f), "rb").read())
+        if h.hexdigest() != ent.get("sha256"):
+            return None
+        return float(ent["bytes_per_launch"])
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+# oracle (CPU) sample
+# ---------------------------------------------------------------------------
+def oracle_sample(workload, bc, full=None):
+    """Time the FP64 oracle on a bounded crop of the workload and scale it to
+    the full workload: per-IB-row build cost x the full workload's IB rows +
+    per-point-step propagation cost x its points x steps.
+    Returns (updates/s for the full workload, description)."""
+    import numpy as np
+    from paper_2309_03600_gb300 import inputs
+    from oracle import sim, stencils
+    if full is None:
+        full = make_workload(workload, bc)
+    if workload == "stag2d":
+        nx = nz = 161
+        nts = 300
+        w = inputs.workload_sinusoid_staggered(nx=nx, nz=nz, h=5.0, M=8, nt=nts, bc=bc)
+        w["src"] = np.array([[400.0, 500.0]])
+        t0 = time.perf_counter()
+        s = sim.Staggered(w["sdf"], w["vel"], w["rho"], 5.0, 8, bc, w["dt"], w["src"], w["rec"][:80])
+        t1 = time.perf_counter()
+        s.forward(w["wavelet"], nts)
+        t2 = time.perf_counter()
+        rows = sum(len(r) for r in s.grad_rows) + len(s.div_rows)
+        g = stencils.Geometry(full["sdf"], full["h"], 8)
+        rows_full = (len(stencils.gradient_ib_nodes(g, 0, 8)) + len(stencils.gradient_ib_nodes(g, 1, 8))
+                     + len(stencils.divergence_ib_nodes(g, 8)))
+    elif workload == "hills3d":
+        nx = ny = 48
+        nz = 40
+        nts = 40
+        prm = inputs.hills_params(3, 3, (nx - 1) * 10.0, (ny - 1) * 10.0, hmin=20, hmax=80, smin=80, smax=200)
+        sdf, zs = inputs.heightfield_sdf_3d(nx, ny, nz, 10.0, inputs.hills_surface(prm, datum=150.0, zmin=40.0))
+        vel = np.full(sdf.shape, 2000.0)
+        dt = 0.45 * 10.0 / 2000.0
+        t0 = time.perf_counter()
+        s = sim.Leapfrog(sdf, vel, 10.0, 8, bc, dt, np.array([[240.0, 240.0, 300.0]]),
+                         np.array([[100.0, 100.0, zs[10, 10] + 20.0]]))
+        t1 = time.perf_counter()
+        s.forward(inputs.ricker(10.0, dt, nts), nts)
+        t2 = time.perf_counter()
+        rows = len(s.rows)
+        rows_full = len(stencils.laplacian_ib_nodes(full["sdf"] > 0, 8))
+        nz = nz
+    else:
+        w = inputs.workload_flat2d(bc=bc)
+        nx, nz = 201, 201
+        nts = 500
+        t0 = time.perf_counter()
+        s = sim.Leapfrog(w["sdf"], w["vel"], w["h"], w["M"], bc, w["dt"], w["src"], w["rec"])
+        t1 = time.perf_counter()
+        s.forward(w["wavelet"], nts)
+        t2 = time.perf_counter()
+        rows = rows_full = len(s.rows)
+    npts = int(np.prod(s.geom.sdf.shape))
+    t_row = (t1 - t0) / max(rows, 1)
+    t_pt = (t2 - t1) / (npts * nts)
+    Nf = grid_points(full)
+    total = t_row * rows_full + t_pt * Nf * full["nt"]
+    desc = ("oracle build (%d IB rows, %.2f s) + %d steps (%.2f s) on a %s crop, scaled to %d IB rows and "
+            "%d points x %d steps" % (rows, t1 - t0, nts, t2 - t1, "x".join(map(str, s.geom.sdf.shape[::-1])),
+                                      rows_full, Nf, full["nt"]))
+    return Nf * full["nt"] / total, desc
+
+
+# ---------------------------------------------------------------------------
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        full = make_workload(args.workload, args.bc)
+        vals, desc = [], ""
+        for i in range(args.warmup + args.steps):
+            v, desc = oracle_sample(args.workload, args.bc, full)
+            if i >= args.warmup:
+                vals.append(v)
+        val = sum(vals) / len(vals)
+        ms = 1e3 * grid_points(full) * full["nt"] / val
+        print(json.dumps({
+            "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": args.workload, "sample": desc},
+            "cpu_baseline": {"kind": "oracle", "value": val, "unit": UNIT, "cores": 1, "sample": desc},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+        return 0
+
+    import numpy as np
+    import torch
+    from paper_2309_03600_gb300 import ib
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    w = make_workload(args.workload, args.bc, rank, args.nt)
+    dtype = torch.float64 if w["dtype"] == "f64" else torch.float32
+    eb = 8 if dtype == torch.float64 else 4
+    nt = w["nt"]
+    sdf_h = torch.as_tensor(w["sdf"], dtype=torch.float64).pin_memory()
+    vel_h = torch.as_tensor(w["vel"], dtype=dtype).pin_memory()
+    rho_h = torch.as_tensor(w["rho"], dtype=dtype).pin_memory() if w.get("rho") is not None else None
+    wav_h = torch.as_tensor(w["wavelet"], dtype=dtype).pin_memory()
+    src_h = torch.as_tensor(w["src"], dtype=torch.float64).pin_memory()
+    rec_h = torch.as_tensor(w["rec"], dtype=torch.float64).pin_memory()
+    sdf, vel, wav, src, rec = (t.to(dev) for t in (sdf_h, vel_h, wav_h, src_h, rec_h))
+    rho = rho_h.to(dev) if rho_h is not None else None
+    M = w["M"]
+    form = w["form"]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
+    traces = torch.zeros((rec.shape[0], nt), dtype=dtype, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        t = ib.ib_build_stencils(sdf, w["h"], w["bc"], form, M)
+        ib.ib_forward(t, vel, wav, src, rec, w["dt"], nt, rho=rho, traces=traces)
+        return t
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        tab = step()
+    torch.cuda.synchronize()
+    stats = tab.stats()
+
+    # ---- timed region: device time per step with events, L2 flushed between steps
+    clocks = Clocks(local)
+    ib.ib_profile_enable(8)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev = []
+    wall0 = time.perf_counter()
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tab = step()
+        e1.record(stream)
+        ev.append((e0, e1))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    prof = ib.ib_profile()
+    ms_steps = [a.elapsed_time(b) for a, b in ev]
+    ms = sum(ms_steps) / len(ms_steps)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    N = grid_points(w)
+    upd_per_step = N * nt
+    value = world * upd_per_step / (ms * 1e-3)
+    launches = sum(d["launches"] for d in prof.values())
+    # ---- roofline of the dominant kernel
+    kb = kernel_bytes(w, stats, eb)
+    dom, dom_t = None, -1.0
+    for name, d in prof.items():
+        if d["sampled"] and name in kb:
+            avg = d["sampled_ms"] / d["sampled"]
+            tot = avg * d["launches"]
+            if tot > dom_t:
+                dom, dom_t = name, tot
+    peak, peak_kind = peaks()
+    roof = None
+    kernels = {}
+    for name, d in prof.items():
+        if d["sampled"]:
+            kernels[name] = {"launches": d["launches"], "avg_us": 1e3 * d["sampled_ms"] / d["sampled"]}
+    if dom:
+        avg_s = prof[dom]["sampled_ms"] / prof[dom]["sampled"] * 1e-3
+        ach = kb[dom] / avg_s / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "peak_kind": peak_kind,
+                "unit": "GB/s", "frac": ach / peak, "traffic": dram_traffic(dom),
+                "algorithmic_bytes_per_launch": kb[dom], "avg_launch_us": avg_s * 1e6,
+                "frac_of_nominal_8TBs": ach / 8000.0}
+    # ---- end to end through the C ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        traces_h = torch.empty((rec.shape[0], nt), dtype=dtype).pin_memory()
+        e2e_ms = []
+        h2d = sum(t.numel() * t.element_size() for t in (sdf_h, vel_h, wav_h, src_h, rec_h) if t is not None)
+        if rho_h is not None:
+            h2d += rho_h.numel() * rho_h.element_size()
+        for _ in range(max(2, min(args.steps, 3))):
+            flush.zero_()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            sd, ve, wa, sr, re_ = (t.to(dev, non_blocking=True) for t in (sdf_h, vel_h, wav_h, src_h, rec_h))
+            rh = rho_h.to(dev, non_blocking=True) if rho_h is not None else None
+            t = ib.ib_build_stencils(sd, w["h"], w["bc"], form, M)
+            tr = ib.ib_forward(t, ve, wa, sr, re_, w["dt"], nt, rho=rh)
+            traces_h.copy_(tr, non_blocking=True)
+            torch.cuda.synchronize()
+            e2e_ms.append(1e3 * (time.perf_counter() - t0))
+        em = sum(e2e_ms) / len(e2e_ms)
+        e2e = {"value": world * upd_per_step / (em * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(traces_h.numel() * traces_h.element_size()), "ms_per_step": em}
+    # ---- CPU oracle baseline (rank 0, one GPU)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        v, desc = oracle_sample(args.workload, args.bc, w)
+        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+    if rank != 0:
+        return 0
+    setup_rows = sum(stats["rows"])
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": w["dtype"], "data": "synthetic",
+        "config": {"workload": args.workload, "desc": w["desc"], "grid": list(w["shape"]), "nt": nt,
+                   "space_order": M, "bc": args.bc, "ib_rows": stats["rows"], "ib_nnz": stats["nnz"],
+                   "l2": "flushed between steps (256 MB write)", "parallelism": "replicas" if world > 1 else "single"},
+        "setup": {"ib_rows": setup_rows, "seconds": stats["setup_seconds"],
+                  "ib_rows_per_s": setup_rows / max(stats["setup_seconds"], 1e-9)},
+        "roofline": roof, "kernels": kernels, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
+        "gpu_launches": int(launches), "wall_s": wall,
+    }
+    print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -207,6 +207,20 @@ ib_status ib_forward_batch(const ib_table* const* tables, const ib_shot* shots,
                            int32_t nshot, int32_t precision, double dt, int32_t nt,
                            void* stream);
 
+/*
+ * Measurement hooks (no counterpart in the paper).  ib_profile_enable(stride)
+ * resets the per-kernel counters; with stride > 0 every stride-th launch of
+ * each time-step kernel is bracketed by CUDA events recorded on its stream.
+ * ib_profile_get(i, ...) returns, for the i-th kernel name seen since the
+ * reset (0 <= i < ib_profile_count()), its launch count, the number of
+ * sampled launches and their summed device time in ms (synchronising on the
+ * sampled events).  Setup kernels are counted, not sampled.
+ */
+ib_status ib_profile_enable(int32_t stride);
+int32_t ib_profile_count(void);
+ib_status ib_profile_get(int32_t i, char* name, int32_t name_len, int64_t* launches,
+                         int64_t* sampled, double* sampled_ms);
+
 /* Synchronise `stream` and return IB_ERR_CUDA on a pending device error. */
 ib_status ib_sync_status(void* stream);
 

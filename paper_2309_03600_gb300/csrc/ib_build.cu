@@ -1188,6 +1188,7 @@ static ib_status run_fit(ib_table* t, const Geo& g, const FitKind& fk, const int
     TRY(tmp.alloc(&flags, L.N));
     k_row_flags<<<grid_for(L.N, 256), 256, 0, s>>>(g, fk.rule, flags);
     IB_CHECK_LAUNCH("k_row_flags");
+            ib_count_launch("setup");
     int64_t* rows = nullptr;
     int64_t nrows = 0;
     TRY(compact(flags, L.N, &rows, &nrows, s));
@@ -1309,6 +1310,7 @@ static ib_status run_fit(ib_table* t, const Geo& g, const FitKind& fk, const int
             int blocks = (int)std::min<int64_t>(nrows, 152 * 16);
             k_fit<<<blocks, FIT_THREADS, shm, s>>>(P);
             IB_CHECK_LAUNCH("k_fit");
+            ib_count_launch("setup");
         }
         IB_CUDA(cudaStreamSynchronize(s));
         // pool overflow?
@@ -1345,6 +1347,7 @@ static ib_status run_fit(ib_table* t, const Geo& g, const FitKind& fk, const int
         if (nrows) {
             k_count_field<<<grid_for(nrows, 256), 256, 0, s>>>(nrows, cnt, start, pool_field, f, fc);
             IB_CHECK_LAUNCH("k_count_field");
+            ib_count_launch("setup");
         }
         TRY(excl_scan(fc, op.row_ptr, nrows + 1, s));
         fptr = op.row_ptr;
@@ -1362,10 +1365,12 @@ static ib_status run_fit(ib_table* t, const Geo& g, const FitKind& fk, const int
             k_pack<<<grid_for(nrows, 32), 32, 0, s>>>(nrows, cnt, start, fptr, pool_code, pool_field, pool_w, f,
                                                        fk.nf, op.col_code, op.w64, op.w32, op.col_pad, L, nullptr);
             IB_CHECK_LAUNCH("k_pack");
+            ib_count_launch("setup");
             IB_CUDA(cudaMemcpyAsync(op.row_lin, rows, sizeof(int64_t) * nrows, cudaMemcpyDeviceToDevice, s));
             IB_CUDA(cudaMemcpyAsync(op.row_info, info, 16 * nrows, cudaMemcpyDeviceToDevice, s));
             k_row_pad<<<grid_for(nrows, 256), 256, 0, s>>>(nrows, rows, L, op.row_pad);
             IB_CHECK_LAUNCH("k_row_pad");
+            ib_count_launch("setup");
         }
         IB_CUDA(cudaStreamSynchronize(s));
         t->table_bytes += nnz * (4 + 8 + 8 + 4) + nrows * (8 + 8 + 8 + 16);
@@ -1688,6 +1693,7 @@ static ib_status make_bins(const Layout& L, int64_t n, const int64_t* pad, int t
     TRY(tmp.alloc(&keys2, n));
     k_tile_keys<<<grid_for(n, 256), 256, 0, s>>>(n, pad, L, tx, ty, tz, ntx, nty, keys, vals);
     IB_CHECK_LAUNCH("k_tile_keys");
+            ib_count_launch("setup");
     size_t tb = 0;
     IB_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tb, keys, keys2, vals, b.perm, (int)n, 0, 32, s));
     void* dt;
@@ -1696,6 +1702,7 @@ static ib_status make_bins(const Layout& L, int64_t n, const int64_t* pad, int t
     IB_CUDA(cub::DeviceRadixSort::SortPairs(dt, tb, keys, keys2, vals, b.perm, (int)n, 0, 32, s));
     k_tile_ptr<<<grid_for(n + 1, 256), 256, 0, s>>>(n, keys2, b.ntiles, b.tile_ptr);
     IB_CHECK_LAUNCH("k_tile_ptr");
+            ib_count_launch("setup");
     IB_CUDA(cudaStreamSynchronize(s));
     return IB_OK;
 }
@@ -1786,6 +1793,7 @@ ib_status ib_table_transpose(ib_table* t, int op, cudaStream_t s) {
     k_expand_entries<<<grid_for(o.nrows, 1), 64, 0, s>>>(o.nrows, o.row_ptr, o.row_pad, o.col_pad, key, idx);
     k_entry_rows<<<grid_for(o.nrows, 1), 64, 0, s>>>(o.nrows, o.row_ptr, erow);
     IB_CHECK_LAUNCH("k_expand_entries");
+            ib_count_launch("setup");
     size_t tb = 0;
     IB_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tb, key, skey, idx, sidx, (int)nnz, 0, 64, s));
     void* dt;
@@ -1800,6 +1808,7 @@ ib_status ib_table_transpose(ib_table* t, int op, cudaStream_t s) {
     k_transpose_fill<<<grid_for(nnz, 256), 256, 0, s>>>(nnz, skey, sidx, erow, o.row_pad, o.w64, o.t_src_off, o.t_w64,
                                                         o.t_w32, head);
     IB_CHECK_LAUNCH("k_transpose_fill");
+            ib_count_launch("setup");
     int64_t* heads;
     int64_t nheads = 0;
     TRY(compact(head, nnz, &heads, &nheads, s));
@@ -1808,6 +1817,7 @@ ib_status ib_table_transpose(ib_table* t, int op, cudaStream_t s) {
     TRY(dalloc(&o.t_ptr, nheads + 1));
     k_transpose_rows<<<grid_for(nheads + 1, 256), 256, 0, s>>>(nheads, heads, skey, nnz, o.t_row_pad, o.t_ptr);
     IB_CHECK_LAUNCH("k_transpose_rows");
+            ib_count_launch("setup");
     IB_CUDA(cudaStreamSynchronize(s));
     o.t_nrows = nheads;
     o.have_t = true;

@@ -125,3 +125,13 @@ ib_status ib_table_bins(ib_table* t, int op, bool transposed, int tx, int ty, in
 ib_status ib_table_transpose(ib_table* t, int op, cudaStream_t s);
 
 double ib_wall_seconds();
+
+// launch counting / sampled timing (ib_prof.cu)
+struct ProfToken {
+    const char* name;
+    bool sampled;
+    cudaEvent_t e0, e1;
+};
+void ib_count_launch(const char* name);
+ProfToken ib_prof_begin(const char* name, cudaStream_t s);
+void ib_prof_end(const ProfToken& t, cudaStream_t s);

@@ -34,6 +34,19 @@ ib_status ib_make_bins_ext(const Layout& L, int64_t n, const int64_t* pad, int t
         if (st_ != IB_OK) return st_;   \
     } while (0)
 
+// sampled event timing around one time-step kernel launch
+#define PROF_LAUNCH(name, stream, ...)                   \
+    do {                                                 \
+        ProfToken tk_ = ib_prof_begin((name), (stream)); \
+        __VA_ARGS__;                                     \
+        ib_prof_end(tk_, (stream));                      \
+    } while (0)
+
+template <typename T>
+static const char* kname(const char* f32, const char* f64) {
+    return sizeof(T) == 8 ? f64 : f32;
+}
+
 // correction table of one operator as seen by a step kernel
 template <typename T>
 struct OpView {
@@ -670,6 +683,7 @@ static ib_status setup_points(const ib_table* t, const ib_shot* sh, double scale
         k_interp_setup<T><<<grid1(sh->nrec, 64), 64, 0, S.s>>>(sh->nrec, sh->rec_dev, d, 1.0 / t->grid.h, L,
                                                                 t->mask_pad[0], 1.0, ri, rw);
     IB_CHECK_LAUNCH("k_interp_setup");
+    ib_count_launch("setup");
     g.src = {sh->nsrc, si, sw};
     g.rec = {sh->nrec, ri, rw};
     return IB_OK;
@@ -698,6 +712,7 @@ static ib_status forward_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, 
     TRY(S.alloc(&K, L.total, true));
     k_leap_coef<T><<<grid1(L.N, 256), 256, 0, s>>>(L, (const T*)sh->vel_dev, t->mask_pad[0], (T)dt, K);
     IB_CHECK_LAUNCH("k_leap_coef");
+    ib_count_launch("setup");
     Geom<T> g;
     TRY(setup_points<T>(t, sh, dt * dt / pow(t->grid.h, d), S, g));
     const TileBins* bins = nullptr;
@@ -740,16 +755,20 @@ static ib_status forward_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, 
         a.step = n;
         a.rec_step = n - 1;
         if (d == 2) {
-            if (H == 1) k_leap2d<T, 1, TX2, TZ2><<<grid2, 256, 0, s>>>(a);
-            else if (H == 2) k_leap2d<T, 2, TX2, TZ2><<<grid2, 256, 0, s>>>(a);
-            else if (H == 3) k_leap2d<T, 3, TX2, TZ2><<<grid2, 256, 0, s>>>(a);
-            else k_leap2d<T, 4, TX2, TZ2><<<grid2, 256, 0, s>>>(a);
+            PROF_LAUNCH(kname<T>("leap2d_f32", "leap2d_f64"), s, {
+                if (H == 1) k_leap2d<T, 1, TX2, TZ2><<<grid2, 256, 0, s>>>(a);
+                else if (H == 2) k_leap2d<T, 2, TX2, TZ2><<<grid2, 256, 0, s>>>(a);
+                else if (H == 3) k_leap2d<T, 3, TX2, TZ2><<<grid2, 256, 0, s>>>(a);
+                else k_leap2d<T, 4, TX2, TZ2><<<grid2, 256, 0, s>>>(a);
+            });
         } else {
             dim3 blk(32, 8);
-            if (H == 1) k_leap3d<T, 1><<<grid3, blk, 0, s>>>(a, zchunk);
-            else if (H == 2) k_leap3d<T, 2><<<grid3, blk, 0, s>>>(a, zchunk);
-            else if (H == 3) k_leap3d<T, 3><<<grid3, blk, 0, s>>>(a, zchunk);
-            else k_leap3d<T, 4><<<grid3, blk, 0, s>>>(a, zchunk);
+            PROF_LAUNCH(kname<T>("leap3d_f32", "leap3d_f64"), s, {
+                if (H == 1) k_leap3d<T, 1><<<grid3, blk, 0, s>>>(a, zchunk);
+                else if (H == 2) k_leap3d<T, 2><<<grid3, blk, 0, s>>>(a, zchunk);
+                else if (H == 3) k_leap3d<T, 3><<<grid3, blk, 0, s>>>(a, zchunk);
+                else k_leap3d<T, 4><<<grid3, blk, 0, s>>>(a, zchunk);
+            });
         }
         IB_CHECK_LAUNCH("leapfrog step");
         std::swap(cur, prev);
@@ -757,6 +776,7 @@ static ib_status forward_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, 
     if (g.rec.n)
         k_receivers<T><<<grid1(g.rec.n, 256), 256, 0, s>>>(g.rec, cur, (T*)sh->traces_dev, nt, nt - 1);
     IB_CHECK_LAUNCH("k_receivers");
+    ib_count_launch("setup");
     return IB_OK;
 }
 
@@ -781,6 +801,7 @@ static ib_status forward_stag(ib_table* t, const ib_shot* sh, double dt, int nt,
     k_stag_coef<T><<<grid1(L.N, 256), 256, 0, s>>>(L, (const T*)sh->vel_dev, (const T*)sh->rho_dev, t->mask_pad[0],
                                                    t->mask_pad[1], t->mask_pad[2], (T)dt, kp, bx, bz);
     IB_CHECK_LAUNCH("k_stag_coef");
+    ib_count_launch("setup");
     Geom<T> g;
     TRY(setup_points<T>(t, sh, dt / pow(t->grid.h, d), S, g));
     const TileBins* b[4];
@@ -812,23 +833,23 @@ static ib_status forward_stag(ib_table* t, const ib_shot* sh, double dt, int nt,
     for (int n = 0; n < nt; ++n) {
         a.step = n;
         a.rec_step = n - 1;
-        if (H == 1) {
-            k_stag_v2d<T, 1, TX2, TZ2><<<grid2, 256, 0, s>>>(a);
-            k_stag_p2d<T, 1, TX2, TZ2><<<grid2, 256, 0, s>>>(a);
-        } else if (H == 2) {
-            k_stag_v2d<T, 2, TX2, TZ2><<<grid2, 256, 0, s>>>(a);
-            k_stag_p2d<T, 2, TX2, TZ2><<<grid2, 256, 0, s>>>(a);
-        } else if (H == 3) {
-            k_stag_v2d<T, 3, TX2, TZ2><<<grid2, 256, 0, s>>>(a);
-            k_stag_p2d<T, 3, TX2, TZ2><<<grid2, 256, 0, s>>>(a);
-        } else {
-            k_stag_v2d<T, 4, TX2, TZ2><<<grid2, 256, 0, s>>>(a);
-            k_stag_p2d<T, 4, TX2, TZ2><<<grid2, 256, 0, s>>>(a);
-        }
+        PROF_LAUNCH(kname<T>("stag_v2d_f32", "stag_v2d_f64"), s, {
+            if (H == 1) k_stag_v2d<T, 1, TX2, TZ2><<<grid2, 256, 0, s>>>(a);
+            else if (H == 2) k_stag_v2d<T, 2, TX2, TZ2><<<grid2, 256, 0, s>>>(a);
+            else if (H == 3) k_stag_v2d<T, 3, TX2, TZ2><<<grid2, 256, 0, s>>>(a);
+            else k_stag_v2d<T, 4, TX2, TZ2><<<grid2, 256, 0, s>>>(a);
+        });
+        PROF_LAUNCH(kname<T>("stag_p2d_f32", "stag_p2d_f64"), s, {
+            if (H == 1) k_stag_p2d<T, 1, TX2, TZ2><<<grid2, 256, 0, s>>>(a);
+            else if (H == 2) k_stag_p2d<T, 2, TX2, TZ2><<<grid2, 256, 0, s>>>(a);
+            else if (H == 3) k_stag_p2d<T, 3, TX2, TZ2><<<grid2, 256, 0, s>>>(a);
+            else k_stag_p2d<T, 4, TX2, TZ2><<<grid2, 256, 0, s>>>(a);
+        });
         IB_CHECK_LAUNCH("staggered step");
     }
     if (g.rec.n) k_receivers<T><<<grid1(g.rec.n, 256), 256, 0, s>>>(g.rec, p, (T*)sh->traces_dev, nt, nt - 1);
     IB_CHECK_LAUNCH("k_receivers");
+    ib_count_launch("setup");
     return IB_OK;
 }
 
@@ -937,6 +958,7 @@ static ib_status adjoint_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, 
     TRY(S.alloc(&grad, L.total, true));
     k_leap_coef<T><<<grid1(L.N, 256), 256, 0, s>>>(L, (const T*)sh->vel_dev, t->mask_pad[0], (T)dt, K);
     IB_CHECK_LAUNCH("k_leap_coef");
+    ib_count_launch("setup");
     Geom<T> g;
     TRY(setup_points<T>(t, sh, dt * dt / pow(t->grid.h, d), S, g));
     const TileBins* fb = nullptr;
@@ -997,10 +1019,12 @@ static ib_status adjoint_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, 
             fa.pm = segbuf + (n - c) * L.total;
             fa.out = segbuf + (n - c + 2) * L.total;
             fa.step = (int)n;
-            if (H == 1) k_leap2d<T, 1, TX2, TZ2><<<grid2, 256, 0, s>>>(fa);
-            else if (H == 2) k_leap2d<T, 2, TX2, TZ2><<<grid2, 256, 0, s>>>(fa);
-            else if (H == 3) k_leap2d<T, 3, TX2, TZ2><<<grid2, 256, 0, s>>>(fa);
-            else k_leap2d<T, 4, TX2, TZ2><<<grid2, 256, 0, s>>>(fa);
+            PROF_LAUNCH(kname<T>("leap2d_f32", "leap2d_f64"), s, {
+                if (H == 1) k_leap2d<T, 1, TX2, TZ2><<<grid2, 256, 0, s>>>(fa);
+                else if (H == 2) k_leap2d<T, 2, TX2, TZ2><<<grid2, 256, 0, s>>>(fa);
+                else if (H == 3) k_leap2d<T, 3, TX2, TZ2><<<grid2, 256, 0, s>>>(fa);
+                else k_leap2d<T, 4, TX2, TZ2><<<grid2, 256, 0, s>>>(fa);
+            });
             IB_CHECK_LAUNCH("recompute step");
         }
         for (int64_t m = e; m >= c + 1; --m) {
@@ -1011,16 +1035,19 @@ static ib_status adjoint_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, 
             aa.pm0 = segbuf + (m - c + 1) * L.total;
             aa.pm1 = segbuf + (m - c) * L.total;
             aa.pm2 = segbuf + (m - c - 1) * L.total;
-            if (H == 1) k_adj2d<T, 1, TX2, TZ2><<<grid2, 256, 0, s>>>(aa);
-            else if (H == 2) k_adj2d<T, 2, TX2, TZ2><<<grid2, 256, 0, s>>>(aa);
-            else if (H == 3) k_adj2d<T, 3, TX2, TZ2><<<grid2, 256, 0, s>>>(aa);
-            else k_adj2d<T, 4, TX2, TZ2><<<grid2, 256, 0, s>>>(aa);
+            PROF_LAUNCH(kname<T>("adj2d_f32", "adj2d_f64"), s, {
+                if (H == 1) k_adj2d<T, 1, TX2, TZ2><<<grid2, 256, 0, s>>>(aa);
+                else if (H == 2) k_adj2d<T, 2, TX2, TZ2><<<grid2, 256, 0, s>>>(aa);
+                else if (H == 3) k_adj2d<T, 3, TX2, TZ2><<<grid2, 256, 0, s>>>(aa);
+                else k_adj2d<T, 4, TX2, TZ2><<<grid2, 256, 0, s>>>(aa);
+            });
             IB_CHECK_LAUNCH("adjoint step");
             std::swap(mu_a, mu_b);
         }
     }
     k_unpad<T><<<grid1(L.N, 256), 256, 0, s>>>(L, grad, grad_out);
     IB_CHECK_LAUNCH("k_unpad");
+    ib_count_launch("setup");
     IB_CUDA(cudaStreamSynchronize(s));
     for (auto& b : keep) {
         cudaFree(b.tile_ptr);

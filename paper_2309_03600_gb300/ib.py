@@ -20,7 +20,7 @@ SECOND_ORDER, FIRST_ORDER_STAGGERED = 0, 1
 
 EXPORTS = ["ib_opts_default", "ib_build_stencils", "ib_table_free", "ib_table_stats", "ib_table_export",
            "ib_forward", "ib_checkpoint_bytes", "ib_adjoint", "ib_forward_batch", "ib_sync_status",
-           "ib_last_error", "ib_version"]
+           "ib_last_error", "ib_version", "ib_profile_enable", "ib_profile_count", "ib_profile_get"]
 
 
 class IbError(RuntimeError):
@@ -94,6 +94,13 @@ def load(path=LIB_PATH):
     L.ib_last_error.restype = ctypes.c_char_p
     L.ib_version.argtypes = []
     L.ib_version.restype = ctypes.c_char_p
+    L.ib_profile_enable.argtypes = [i32]
+    L.ib_profile_enable.restype = i32
+    L.ib_profile_count.argtypes = []
+    L.ib_profile_count.restype = i32
+    L.ib_profile_get.argtypes = [i32, ctypes.c_char_p, i32, ctypes.POINTER(i64), ctypes.POINTER(i64),
+                                 ctypes.POINTER(dbl)]
+    L.ib_profile_get.restype = i32
     _LIB = L
     return L
 
@@ -263,6 +270,27 @@ def ib_last_error():
 
 def ib_version():
     return load().ib_version().decode()
+
+
+def ib_profile_enable(stride):
+    return _check(load().ib_profile_enable(int(stride)))
+
+
+def ib_profile_count():
+    return int(load().ib_profile_count())
+
+
+def ib_profile_get(i):
+    name = ctypes.create_string_buffer(64)
+    la, sa = ctypes.c_int64(), ctypes.c_int64()
+    ms = ctypes.c_double()
+    _check(load().ib_profile_get(int(i), name, 64, ctypes.byref(la), ctypes.byref(sa), ctypes.byref(ms)))
+    return dict(name=name.value.decode(), launches=la.value, sampled=sa.value, sampled_ms=ms.value)
+
+
+def ib_profile():
+    """All kernels seen since the last ib_profile_enable: name -> counters."""
+    return {d["name"]: d for d in (ib_profile_get(i) for i in range(ib_profile_count()))}
 
 
 class Forward(torch.autograd.Function):
