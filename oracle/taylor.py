@@ -204,7 +204,13 @@ def bc_rows_vector(bc, d, M, normal):
 
     Each row is a list of d operators, one per component block.
     free : lap^k div v = 0 for 2k+1 <= M.
-    rigid: n . v = 0, and n . grad lap^k div v = 0 for 2k+2 <= M.
+    rigid: n . v = 0, and n . grad lap^k div v = 0 for 2k+2 <= M (zero normal
+           velocity and its time derivatives), plus lap^k curl v = 0 for
+           2k+1 <= M: the acoustic velocity of the first-order system is
+           irrotational (v_t = grad p / rho with constant rho), which fixes the
+           tangential extrapolation.  Reading: the paper gives no velocity
+           conditions for a rigid surface; without the curl rows the staggered
+           rigid scheme grows exponentially on a sinusoidal surface.
     """
     L = op_laplacian(d)
     rows = []
@@ -224,9 +230,23 @@ def bc_rows_vector(bc, d, M, normal):
                 nd = op_add(nd, op_partial(d, b), float(normal[b]))
             rows.append([op_mul(op_mul(nd, op_partial(d, a)), Lk) for a in range(d)])
             k += 1
+        k = 0
+        while 2 * k + 1 <= M:
+            Lk = op_power(L, k, d)
+            for (i, j) in _curl_pairs(d):
+                row = [{} for _ in range(d)]
+                row[j] = op_mul(op_partial(d, i), Lk)
+                row[i] = op_scale(op_mul(op_partial(d, j), Lk), -1.0)
+                rows.append(row)
+            k += 1
     else:
         raise ValueError(bc)
     return rows
+
+
+def _curl_pairs(d):
+    """Index pairs (i, j) of the curl components d_i v_j - d_j v_i."""
+    return [(0, 1)] if d == 2 else [(1, 2), (2, 0), (0, 1)]
 
 
 # ---------------------------------------------------------------------------
@@ -317,6 +337,15 @@ def bc_templates_vector(bc, d, M):
             Lk = op_power(L, k, d)
             rows.append([[(b, op_mul(op_mul(op_partial(d, b), op_partial(d, a)), Lk)) for b in range(d)]
                          for a in range(d)])
+            k += 1
+        k = 0
+        while 2 * k + 1 <= M:
+            Lk = op_power(L, k, d)
+            for (i, j) in _curl_pairs(d):
+                row = [[] for _ in range(d)]
+                row[j].append((None, op_mul(op_partial(d, i), Lk)))
+                row[i].append((None, op_scale(op_mul(op_partial(d, j), Lk), -1.0)))
+                rows.append(row)
             k += 1
     else:
         raise ValueError(bc)

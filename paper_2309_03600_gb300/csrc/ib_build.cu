@@ -258,6 +258,22 @@ static HostTemplate bc_template(bool vector, ib_bc bc, int d, int M) {
                         add_terms(row, op_mul(op_mul(op_d(b), op_d(a)), op_pow(L, k)), a, b);
                 T.rows.push_back(row);
             }
+            // irrotational acoustic velocity: lap^k (d_i v_j - d_j v_i) = 0, 2k + 1 <= M
+            const int pairs2[1][2] = {{0, 1}};
+            const int pairs3[3][2] = {{1, 2}, {2, 0}, {0, 1}};
+            for (int k = 0; 2 * k + 1 <= M; ++k) {
+                int np = d == 2 ? 1 : 3;
+                for (int q = 0; q < np; ++q) {
+                    int i = d == 2 ? pairs2[q][0] : pairs3[q][0];
+                    int j = d == 2 ? pairs2[q][1] : pairs3[q][1];
+                    std::vector<DevTerm> row;
+                    add_terms(row, op_mul(op_d(i), op_pow(L, k)), j, -1);
+                    Op neg = op_mul(op_d(j), op_pow(L, k));
+                    for (auto& t : neg) t.second = -t.second;
+                    add_terms(row, neg, i, -1);
+                    T.rows.push_back(row);
+                }
+            }
         }
     }
     return T;
@@ -1383,14 +1399,8 @@ static void free_op(IbOp& op) {
                   op.t_row_pad, op.t_ptr, op.t_src_off, op.t_w64, op.t_w32};
     for (void* p : ps)
         if (p) cudaFree(p);
-    for (auto& b : op.bins) {
-        cudaFree(b.tile_ptr);
-        cudaFree(b.perm);
-    }
-    for (auto& b : op.t_bins) {
-        cudaFree(b.tile_ptr);
-        cudaFree(b.perm);
-    }
+    for (auto& b : op.bins) ib_free_bins(b);
+    for (auto& b : op.t_bins) ib_free_bins(b);
     op = IbOp();
 }
 
@@ -1652,7 +1662,7 @@ __global__ void k_tile_keys(int64_t n, const int64_t* pad, Layout L, int tx, int
                             int64_t nty, int32_t* keys, int32_t* vals) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         int64_t q = pad[i] - L.base;
-        int64_t z = (q >= 0 ? q : q - L.plane + 1) / L.plane;
+        int64_t z = q / L.plane;
         int64_t rem = q - z * L.plane;
         int64_t y = rem / L.px;
         int64_t x = rem - y * L.px;
@@ -1671,7 +1681,60 @@ __global__ void k_tile_ptr(int64_t n, const int32_t* sorted_keys, int64_t ntiles
     }
 }
 
-static ib_status make_bins(const Layout& L, int64_t n, const int64_t* pad, int tx, int ty, int tz, TileBins& b,
+__global__ void k_perm_nnz(int64_t n, const int32_t* perm, const int64_t* row_ptr, int64_t* cnt) {
+    for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        int32_t r = perm[k];
+        cnt[k] = row_ptr[r + 1] - row_ptr[r];
+    }
+}
+
+__global__ void k_ent_ptr(int64_t ntiles, const int32_t* tile_ptr, const int64_t* ent_off, int32_t* ent_ptr) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t <= ntiles; t += (int64_t)gridDim.x * blockDim.x)
+        ent_ptr[t] = (int32_t)ent_off[tile_ptr[t]];
+}
+
+// one block per row (in tile order): expand its entries relative to the tile origin
+__global__ void k_fill_entries(int64_t n, const int32_t* perm, const int32_t* sorted_keys, const int64_t* ent_off,
+                               const int64_t* row_pad, const int64_t* row_ptr, const int64_t* col_pad,
+                               const double* w64, Layout L, TileBins b, int32_t* loc, int32_t* src, float* w32o,
+                               double* w64o) {
+    for (int64_t k = blockIdx.x; k < n; k += gridDim.x) {
+        const int32_t r = perm[k];
+        const int64_t org = tile_origin(L, b, sorted_keys[k]);
+        const int64_t q = row_pad[r];
+        const int64_t rel = q - org;
+        int32_t lx, ly;
+        if (L.ndim == 2) {
+            int64_t dz = rel >= 0 ? rel / L.px : -((-rel + L.px - 1) / L.px);
+            ly = (int32_t)dz;
+            lx = (int32_t)(rel - dz * L.px);
+        } else {
+            int64_t dy = rel / L.px;
+            ly = (int32_t)dy;
+            lx = (int32_t)(rel - dy * L.px);
+        }
+        const int32_t lidx = ly * b.tx + lx;
+        const int64_t o = ent_off[k];
+        const int64_t j0 = row_ptr[r];
+        for (int64_t j = j0 + threadIdx.x; j < row_ptr[r + 1]; j += blockDim.x) {
+            loc[o + (j - j0)] = lidx;
+            src[o + (j - j0)] = (int32_t)(rel + col_pad[j]);
+            w32o[o + (j - j0)] = (float)w64[j];
+            w64o[o + (j - j0)] = w64[j];
+        }
+    }
+}
+
+void ib_free_bins(TileBins& b) {
+    void* ps[] = {b.tile_ptr, b.perm, b.ent_ptr, b.ent_loc, b.ent_src, b.ent_w32, b.ent_w64};
+    for (void* p : ps)
+        if (p) cudaFree(p);
+    b = TileBins();
+}
+
+// rows (row_pad) binned by tile; with row_ptr/col_pad/w64 also the flattened entries
+static ib_status make_bins(const Layout& L, int64_t n, const int64_t* pad, const int64_t* row_ptr,
+                           const int64_t* col_pad, const double* w64, int tx, int ty, int tz, TileBins& b,
                            cudaStream_t s) {
     int64_t ntx = (L.nx + tx - 1) / tx;
     int64_t nty = (L.ny + ty - 1) / ty;
@@ -1679,11 +1742,20 @@ static ib_status make_bins(const Layout& L, int64_t n, const int64_t* pad, int t
     b.tx = tx;
     b.ty = ty;
     b.tz = tz;
+    b.ntx = ntx;
+    b.nty = nty;
     b.ntiles = ntx * nty * ntz;
     TRY(dalloc(&b.tile_ptr, b.ntiles + 1));
     TRY(dalloc(&b.perm, std::max<int64_t>(n, 1)));
+    TRY(dalloc(&b.ent_ptr, b.ntiles + 1));
     if (n == 0) {
         IB_CUDA(cudaMemsetAsync(b.tile_ptr, 0, sizeof(int32_t) * (b.ntiles + 1), s));
+        IB_CUDA(cudaMemsetAsync(b.ent_ptr, 0, sizeof(int32_t) * (b.ntiles + 1), s));
+        TRY(dalloc(&b.ent_loc, 1));
+        TRY(dalloc(&b.ent_src, 1));
+        TRY(dalloc(&b.ent_w32, 1));
+        TRY(dalloc(&b.ent_w64, 1));
+        IB_CUDA(cudaStreamSynchronize(s));
         return IB_OK;
     }
     DevBuf tmp;
@@ -1693,7 +1765,7 @@ static ib_status make_bins(const Layout& L, int64_t n, const int64_t* pad, int t
     TRY(tmp.alloc(&keys2, n));
     k_tile_keys<<<grid_for(n, 256), 256, 0, s>>>(n, pad, L, tx, ty, tz, ntx, nty, keys, vals);
     IB_CHECK_LAUNCH("k_tile_keys");
-            ib_count_launch("setup");
+    ib_count_launch("setup");
     size_t tb = 0;
     IB_CUDA(cub::DeviceRadixSort::SortPairs(nullptr, tb, keys, keys2, vals, b.perm, (int)n, 0, 32, s));
     void* dt;
@@ -1702,14 +1774,39 @@ static ib_status make_bins(const Layout& L, int64_t n, const int64_t* pad, int t
     IB_CUDA(cub::DeviceRadixSort::SortPairs(dt, tb, keys, keys2, vals, b.perm, (int)n, 0, 32, s));
     k_tile_ptr<<<grid_for(n + 1, 256), 256, 0, s>>>(n, keys2, b.ntiles, b.tile_ptr);
     IB_CHECK_LAUNCH("k_tile_ptr");
-            ib_count_launch("setup");
+    ib_count_launch("setup");
+    if (row_ptr) {
+        int64_t *cnt, *off;
+        TRY(tmp.alloc(&cnt, n + 1));
+        TRY(tmp.alloc(&off, n + 1));
+        IB_CUDA(cudaMemsetAsync(cnt + n, 0, sizeof(int64_t), s));
+        k_perm_nnz<<<grid_for(n, 256), 256, 0, s>>>(n, b.perm, row_ptr, cnt);
+        IB_CHECK_LAUNCH("k_perm_nnz");
+        TRY(excl_scan(cnt, off, n + 1, s));
+        IB_CUDA(cudaMemcpy(&b.nent, off + n, sizeof(int64_t), cudaMemcpyDeviceToHost));
+        if (b.nent >= (int64_t)1 << 31) {
+            ib_set_error("correction table too large for 32-bit tile entry offsets");
+            return IB_ERR_ARG;
+        }
+        TRY(dalloc(&b.ent_loc, std::max<int64_t>(b.nent, 1)));
+        TRY(dalloc(&b.ent_src, std::max<int64_t>(b.nent, 1)));
+        TRY(dalloc(&b.ent_w32, std::max<int64_t>(b.nent, 1)));
+        TRY(dalloc(&b.ent_w64, std::max<int64_t>(b.nent, 1)));
+        k_ent_ptr<<<grid_for(b.ntiles + 1, 256), 256, 0, s>>>(b.ntiles, b.tile_ptr, off, b.ent_ptr);
+        k_fill_entries<<<grid_for(n, 1), 64, 0, s>>>(n, b.perm, keys2, off, pad, row_ptr, col_pad, w64, L, b,
+                                                     b.ent_loc, b.ent_src, b.ent_w32, b.ent_w64);
+        IB_CHECK_LAUNCH("k_fill_entries");
+        ib_count_launch("setup");
+    } else {
+        IB_CUDA(cudaMemsetAsync(b.ent_ptr, 0, sizeof(int32_t) * (b.ntiles + 1), s));
+    }
     IB_CUDA(cudaStreamSynchronize(s));
     return IB_OK;
 }
 
 ib_status ib_make_bins_ext(const Layout& L, int64_t n, const int64_t* pad, int tx, int ty, int tz, TileBins& b,
                            cudaStream_t s) {
-    return make_bins(L, n, pad, tx, ty, tz, b, s);
+    return make_bins(L, n, pad, nullptr, nullptr, nullptr, tx, ty, tz, b, s);
 }
 
 ib_status ib_table_bins(ib_table* t, int op, bool transposed, int tx, int ty, int tz, const TileBins** out,
@@ -1722,8 +1819,12 @@ ib_status ib_table_bins(ib_table* t, int op, bool transposed, int tx, int ty, in
             return IB_OK;
         }
     TileBins b;
-    if (transposed) TRY(make_bins(t->L, o.t_nrows, o.t_row_pad, tx, ty, tz, b, s));
-    else TRY(make_bins(t->L, o.nrows, o.row_pad, tx, ty, tz, b, s));
+    if (transposed) {
+        TRY(ib_table_transpose(t, op, s));
+        TRY(make_bins(t->L, o.t_nrows, o.t_row_pad, o.t_ptr, o.t_src_off, o.t_w64, tx, ty, tz, b, s));
+    } else {
+        TRY(make_bins(t->L, o.nrows, o.row_pad, o.row_ptr, o.col_pad, o.w64, tx, ty, tz, b, s));
+    }
     v.push_back(b);
     *out = &v.back();
     return IB_OK;

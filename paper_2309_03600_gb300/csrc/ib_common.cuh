@@ -77,9 +77,30 @@ __host__ __device__ inline void unpack_off(int32_t c, int& dx, int& dy, int& dz)
 struct TileBins {             // rows of one operator binned by step tile
     int tx = 0, ty = 0, tz = 0;
     int64_t ntiles = 0;
+    int64_t ntx = 0, nty = 0;
     int32_t* tile_ptr = nullptr;   // [ntiles + 1]
     int32_t* perm = nullptr;       // [nrows] row ids grouped by tile
+    // the corrections flattened per tile: entry e of tile t adds
+    // w[e] * f[origin(t) + src[e]] to output loc[e] of the tile
+    int64_t nent = 0;
+    int32_t* ent_ptr = nullptr;    // [ntiles + 1]
+    int32_t* ent_loc = nullptr;    // local output index (row-major inside the tile)
+    int32_t* ent_src = nullptr;    // source offset from the tile origin (padded index)
+    float* ent_w32 = nullptr;
+    double* ent_w64 = nullptr;
 };
+
+// padded index of the first node of a tile (2D: (bx, bz); 3D: (bx, by, z))
+__host__ __device__ inline int64_t tile_origin(const Layout& L, const TileBins& b, int64_t tile) {
+    int64_t bx = tile % b.ntx;
+    int64_t r = tile / b.ntx;
+    int64_t by = r % b.nty;
+    int64_t bz = r / b.nty;
+    if (L.ndim == 2) return L.base + bz * b.tz * L.px + bx * b.tx;
+    return L.base + bz * b.tz * L.plane + by * b.ty * L.px + bx * b.tx;
+}
+
+void ib_free_bins(TileBins& b);
 
 struct IbOp {
     int64_t nrows = 0, nnz = 0;

@@ -1,6 +1,6 @@
-// Time stepping: fused leapfrog (2D, 3D), staggered pressure-velocity (2D),
-// source injection, receiver interpolation, the exact discrete adjoint and
-// checkpointed velocity gradients.
+// Time stepping: fused leapfrog (2D, 3D, batched 2D), staggered
+// pressure-velocity (2D), source injection, receiver interpolation, the exact
+// discrete adjoint and checkpointed velocity gradients.
 //
 // Paper: p^{t+1} = 2p^t - p^{t-1} + dt^2 c^2 lap p + dt^2 f (2nd-order
 // application section), first-order system with the paper's signs and a
@@ -8,17 +8,25 @@
 // the boundary ("Reconciliation with the Interior Numerical Discretization"),
 // zero Dirichlet outer edges (Examples section).
 //
-// Every step kernel works on a tile of outputs: the bulk stencil reads a
-// shared-memory copy of the tile and its halo; the immersed-boundary rows that
-// fall in the tile are then added by a warp-cooperative gather over the
-// correction table (one warp per row, lanes over the row's entries); finally
-// the update, source injection and masking are applied and the tile is written.
+// Every step kernel owns a tile of outputs.  The bulk stencil reads a
+// shared-memory copy of the tile and its halo.  The immersed-boundary
+// corrections of the tile's rows are stored flattened per tile (output slot,
+// source offset, weight) and are added by all threads of the block with
+// shared-memory atomics -- a balanced, coalesced gather whatever the number of
+// IB rows in the tile.  The update, source injection and masking follow, and
+// the tile is written once.
+//
+// Arithmetic: coefficients (dt^2 c^2 / h^2, dt rho c^2 / h, dt / (rho h)) are
+// formed in FP64 and rounded once; the leapfrog update is evaluated as
+// p + ((p - p_prev) + Kh * lap) to keep one rounding at the field's magnitude.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "ib_common.cuh"
@@ -47,35 +55,65 @@ static const char* kname(const char* f32, const char* f64) {
     return sizeof(T) == 8 ? f64 : f32;
 }
 
-// correction table of one operator as seen by a step kernel
+// flattened corrections of one operator for one tile shape
 template <typename T>
-struct OpView {
+struct TileView {
+    const int32_t* ptr;    // [ntiles + 1]
+    const int32_t* loc;
+    const int32_t* src;
+    const T* w;
+    int64_t ntx;
+};
+
+template <typename T>
+struct PointSet {          // multilinear weights: 8 corner slots per point
+    int n;
+    const int64_t* idx;    // padded node
+    const T* w;
+};
+
+// rows of a small gather table (receiver residual injection in the adjoint)
+template <typename T>
+struct RowView {
     const int64_t* row_pad;
     const int64_t* row_ptr;
-    const int64_t* col_pad;
+    const int64_t* col;
     const T* w;
     const int32_t* tile_ptr;
     const int32_t* perm;
-    int64_t ntx, nty;
+    int64_t ntx;
 };
 
 template <typename T>
-struct PointSet {                 // multilinear weights: 8 corner slots per point
-    int n;
-    const int64_t* idx;           // padded node
-    const T* w;
-};
+__device__ __forceinline__ void add_entries(const TileView<T>& v, int64_t tile, const T* f, int64_t origin, T* acc,
+                                            int tid, int nthr) {
+    const int32_t e0 = v.ptr[tile], e1 = v.ptr[tile + 1];
+    for (int32_t e = e0 + tid; e < e1; e += nthr) atomicAdd(&acc[v.loc[e]], v.w[e] * f[origin + v.src[e]]);
+}
 
+template <typename T>
+__device__ __forceinline__ void record_receivers(const PointSet<T>& rec, const T* p, T* traces, int nt, int col,
+                                                 int64_t gid) {
+    if (col >= 0 && gid < rec.n) {
+        T s = 0;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) s += rec.w[8 * gid + c] * p[rec.idx[8 * gid + c]];
+        traces[gid * nt + col] = s;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// second-order leapfrog
+// ---------------------------------------------------------------------------
 template <typename T>
 struct StepArgs {
     Layout L;
     T w2[5];             // central 2nd-derivative weights w[0..H]
-    const T* p;          // current field p^n
-    const T* pm;         // previous field p^{n-1}
+    const T* p;          // p^n
+    const T* pm;         // p^{n-1}
     T* out;              // p^{n+1} (may alias pm)
-    const T* K;          // dt^2 c^2 (0 outside the domain)
-    T inv_h2;
-    OpView<T> op;
+    const T* Kh;         // dt^2 c^2 / h^2 (0 outside the domain)
+    TileView<T> op;
     PointSet<T> src;     // weights include dt^2 / h^d
     const T* wavelet;
     int step;
@@ -83,58 +121,18 @@ struct StepArgs {
     T* traces;
     int nt;
     int rec_step;        // trace column written from p (-1: none)
+    // batched runs: the two wavefield buffers (p^n is buf[step & 1])
+    T* buf0;
+    T* buf1;
+    int64_t ntx;         // tiles along x
+    int64_t ntiles;      // tiles of the shot (blocks beyond only record receivers)
 };
 
-template <typename T>
-__device__ __forceinline__ void record_receivers(const PointSet<T>& rec, const T* p, T* traces, int nt, int col) {
-    int gid = (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    gid = gid * (blockDim.x * blockDim.y) + threadIdx.y * blockDim.x + threadIdx.x;
-    if (col >= 0 && gid < rec.n) {
-        T s = 0;
-#pragma unroll
-        for (int c = 0; c < 8; ++c) s += rec.w[8 * gid + c] * p[rec.idx[8 * gid + c]];
-        traces[(int64_t)gid * nt + col] = s;
-    }
-}
-
-// one warp per IB row of the tile: acc[local] += sum_k w_k f[row + col_k]
-template <typename T, int TXA>
-__device__ __forceinline__ void gather_rows(const OpView<T>& op, int64_t tile, const T* f, const Layout& L, int64_t x0,
-                                            int64_t y0, T* acc, int accy) {
-    const int warp = (threadIdx.y * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    const int nw = (blockDim.x * blockDim.y) >> 5;
-    const int32_t b = op.tile_ptr[tile], e = op.tile_ptr[tile + 1];
-    for (int k = b + warp; k < e; k += nw) {
-        const int32_t r = op.perm[k];
-        const int64_t q = op.row_pad[r];
-        T s = 0;
-        for (int64_t j = op.row_ptr[r] + lane; j < op.row_ptr[r + 1]; j += 32) s += op.w[j] * f[q + op.col_pad[j]];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-        if (lane == 0) {
-            int64_t loc = q - L.base;
-            int64_t z = loc / L.plane;
-            int64_t rem = loc - z * L.plane;
-            int64_t y = rem / L.px;
-            int64_t x = rem - y * L.px;
-            if (L.ndim == 2) y = z;   // 2D: tile rows are z
-            acc[(y - y0) * TXA + (x - x0)] += s;
-        }
-    }
-    (void)accy;
-}
-
-// ---------------------------------------------------------------------------
-// 2D leapfrog: tile TX x TZ, 256 threads (TX/32 outputs per thread per row)
-// ---------------------------------------------------------------------------
 template <typename T, int H, int TX, int TZ>
-__global__ void __launch_bounds__(256) k_leap2d(StepArgs<T> a) {
-    __shared__ T tile[TZ + 2 * H][TX + 2 * H];
-    __shared__ T acc[TZ * TX];
+__device__ __forceinline__ void leap2d_tile(const StepArgs<T>& a, int64_t bx, int64_t bz, T (*tile)[TX + 2 * H],
+                                            T* acc) {
     const int tid = threadIdx.x;
-    record_receivers(a.rec, a.p, a.traces, a.nt, a.rec_step);
-    const int64_t x0 = (int64_t)blockIdx.x * TX, z0 = (int64_t)blockIdx.y * TZ;
+    const int64_t x0 = bx * TX, z0 = bz * TZ;
     const Layout& L = a.L;
     for (int i = tid; i < (TZ + 2 * H) * (TX + 2 * H); i += 256) {
         int lz = i / (TX + 2 * H), lx = i - lz * (TX + 2 * H);
@@ -151,44 +149,81 @@ __global__ void __launch_bounds__(256) k_leap2d(StepArgs<T> a) {
 #pragma unroll
         for (int k = 1; k <= H; ++k)
             s += a.w2[k] * ((tile[lz + H][lx + H + k] + tile[lz + H][lx + H - k]) +
-                             (tile[lz + H + k][lx + H] + tile[lz + H - k][lx + H]));
+                            (tile[lz + H + k][lx + H] + tile[lz + H - k][lx + H]));
         acc[i] = s;
     }
     __syncthreads();
-    if (a.op.tile_ptr) gather_rows<T, TX>(a.op, (int64_t)blockIdx.y * a.op.ntx + blockIdx.x, a.p, L, x0, z0, acc, TZ);
+    const int64_t origin = L.base + z0 * L.px + x0;
+    if (a.op.ptr) add_entries(a.op, bz * a.op.ntx + bx, a.p, origin, acc, tid, 256);
     __syncthreads();
     const T wv = a.src.n ? a.wavelet[a.step] : (T)0;
     for (int i = tid; i < TZ * TX; i += 256) {
         int lz = i / TX, lx = i - lz * TX;
         int64_t x = x0 + lx, z = z0 + lz;
         if (x >= L.nx || z >= L.nz) continue;
-        int64_t q = L.base + z * L.px + x;
-        T v = (T)2 * tile[lz + H][lx + H] - a.pm[q] + a.K[q] * (acc[i] * a.inv_h2);
+        int64_t q = origin + lz * L.px + lx;
+        T c = tile[lz + H][lx + H];
+        T v = c + ((c - a.pm[q]) + a.Kh[q] * acc[i]);
         for (int s = 0; s < 8 * a.src.n; ++s)
             if (a.src.idx[s] == q) v += a.src.w[s] * wv;
         a.out[q] = v;
     }
 }
 
+template <typename T, int H, int TX, int TZ>
+__global__ void __launch_bounds__(256) k_leap2d(StepArgs<T> a) {
+    __shared__ T tile[TZ + 2 * H][TX + 2 * H];
+    __shared__ T acc[TZ * TX];
+    const int64_t blk = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+    record_receivers(a.rec, a.p, a.traces, a.nt, a.rec_step, blk * 256 + threadIdx.x);
+    leap2d_tile<T, H, TX, TZ>(a, blockIdx.x, blockIdx.y, tile, acc);
+}
+
+// many shots in one launch: block -> (shot, tile) through the per-shot tile offsets
+template <typename T, int H, int TX, int TZ>
+__global__ void __launch_bounds__(256) k_leap2d_batch(const StepArgs<T>* __restrict__ shots,
+                                                      const int64_t* __restrict__ tile0, int nshot, int step) {
+    __shared__ T tile[TZ + 2 * H][TX + 2 * H];
+    __shared__ T acc[TZ * TX];
+    const int64_t b = blockIdx.x;
+    int lo = 0, hi = nshot - 1;
+    while (lo < hi) {                     // last shot with tile0[s] <= b
+        int mid = (lo + hi + 1) >> 1;
+        if (tile0[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    StepArgs<T> a = shots[lo];
+    const int64_t local = b - tile0[lo];
+    T* cur = (step & 1) ? a.buf1 : a.buf0;
+    T* prev = (step & 1) ? a.buf0 : a.buf1;
+    a.p = cur;
+    a.pm = prev;
+    a.out = prev;
+    a.step = step;
+    a.rec_step = step - 1;
+    record_receivers(a.rec, a.p, a.traces, a.nt, a.rec_step, local * 256 + threadIdx.x);
+    if (local >= a.ntiles) return;   // uniform per block
+    leap2d_tile<T, H, TX, TZ>(a, local % a.ntx, local / a.ntx, tile, acc);
+}
+
 // receivers only (after the last step)
 template <typename T>
 __global__ void k_receivers(PointSet<T> rec, const T* p, T* traces, int nt, int col) {
-    record_receivers(rec, p, traces, nt, col);
+    record_receivers(rec, p, traces, nt, col, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
 }
 
-// ---------------------------------------------------------------------------
-// 3D leapfrog: (x, y) tile of 32 x 8 columns marching in z with a register
-// queue of the 2H + 1 values of its own column; x/y neighbours from a
-// shared-memory copy of the current plane with its halo.
-// ---------------------------------------------------------------------------
+// 3D: (x, y) tile of 32 x 8 columns marching in z with a register queue of the
+// 2H + 1 values of its own column; x/y neighbours from a shared-memory copy of
+// the current plane with its halo.
 template <typename T, int H>
-__global__ void __launch_bounds__(256) k_leap3d(StepArgs<T> a, int zchunk) {
+__global__ void __launch_bounds__(256) k_leap3d(StepArgs<T> a, int zchunk, int64_t nty) {
     constexpr int TX = 32, TY = 8;
     __shared__ T tile[TY + 2 * H][TX + 2 * H];
     __shared__ T acc[TY * TX];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * TX + tx;
-    record_receivers(a.rec, a.p, a.traces, a.nt, a.rec_step);
+    const int64_t blk = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    record_receivers(a.rec, a.p, a.traces, a.nt, a.rec_step, blk * 256 + tid);
     const Layout& L = a.L;
     const int64_t x0 = (int64_t)blockIdx.x * TX, y0 = (int64_t)blockIdx.y * TY;
     const int64_t x = x0 + tx, y = y0 + ty;
@@ -214,16 +249,17 @@ __global__ void __launch_bounds__(256) k_leap3d(StepArgs<T> a, int zchunk) {
 #pragma unroll
             for (int k = 1; k <= H; ++k)
                 s += a.w2[k] * ((tile[ty + H][tx + H + k] + tile[ty + H][tx + H - k]) +
-                                 (tile[ty + H + k][tx + H] + tile[ty + H - k][tx + H]) + (q[H + k] + q[H - k]));
+                                (tile[ty + H + k][tx + H] + tile[ty + H - k][tx + H]) + (q[H + k] + q[H - k]));
             acc[tid] = s;
         }
         __syncthreads();
-        if (a.op.tile_ptr)
-            gather_rows<T, TX>(a.op, (z * a.op.nty + blockIdx.y) * a.op.ntx + blockIdx.x, a.p, L, x0, y0, acc, TY);
+        const int64_t origin = L.idx(x0, y0, z);
+        if (a.op.ptr) add_entries(a.op, (z * nty + blockIdx.y) * a.op.ntx + blockIdx.x, a.p, origin, acc, tid, 256);
         __syncthreads();
         if (valid) {
             int64_t qi = L.idx(x, y, z);
-            T v = (T)2 * q[H] - a.pm[qi] + a.K[qi] * (acc[tid] * a.inv_h2);
+            T c = q[H];
+            T v = c + ((c - a.pm[qi]) + a.Kh[qi] * acc[tid]);
             for (int s = 0; s < 8 * a.src.n; ++s)
                 if (a.src.idx[s] == qi) v += a.src.w[s] * wv;
             a.out[qi] = v;
@@ -238,8 +274,9 @@ __global__ void __launch_bounds__(256) k_leap3d(StepArgs<T> a, int zchunk) {
 
 // ---------------------------------------------------------------------------
 // 2D staggered pressure-velocity
-//   v_a[j] (at j + e_a/2) += b_a[j] (sum_k c_k (p[j + k e_a] - p[j - (k-1) e_a]) + IB) / h
-//   p[j] += kp[j] (sum_a sum_k c_k (v_a[j + (k-1) e_a] - v_a[j - k e_a]) + IB) / h + src
+//   v_a[j] (at j + e_a/2) += bh_a[j] (sum_k c_k (p[j + k e_a] - p[j - (k-1) e_a]) + IB)
+//   p[j] += kh[j] (sum_a sum_k c_k (v_a[j + (k-1) e_a] - v_a[j - k e_a]) + IB) + src
+// with bh_a = dt / (rho h) and kh = dt rho c^2 / h
 // ---------------------------------------------------------------------------
 template <typename T>
 struct StagArgs {
@@ -248,12 +285,11 @@ struct StagArgs {
     T* p;
     T* vx;
     T* vz;
-    const T* bx;      // dt / rho at v_x nodes (0 outside)
+    const T* bx;
     const T* bz;
-    const T* kp;      // dt rho c^2 at p nodes (0 outside)
-    T inv_h;
-    OpView<T> gx, gz, dx, dz;
-    PointSet<T> src;  // weights include dt / h^d
+    const T* kp;
+    TileView<T> gx, gz, dx, dz;
+    PointSet<T> src;     // weights include dt / h^d
     const T* wavelet;
     int step;
     PointSet<T> rec;
@@ -268,7 +304,8 @@ __global__ void __launch_bounds__(256) k_stag_v2d(StagArgs<T> a) {
     __shared__ T ax[TZ * TX];
     __shared__ T az[TZ * TX];
     const int tid = threadIdx.x;
-    record_receivers(a.rec, a.p, a.traces, a.nt, a.rec_step);
+    const int64_t blk = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+    record_receivers(a.rec, a.p, a.traces, a.nt, a.rec_step, blk * 256 + tid);
     const int64_t x0 = (int64_t)blockIdx.x * TX, z0 = (int64_t)blockIdx.y * TZ;
     const Layout& L = a.L;
     for (int i = tid; i < (TZ + 2 * H) * (TX + 2 * H); i += 256) {
@@ -292,16 +329,17 @@ __global__ void __launch_bounds__(256) k_stag_v2d(StagArgs<T> a) {
     }
     __syncthreads();
     const int64_t tile_id = (int64_t)blockIdx.y * a.gx.ntx + blockIdx.x;
-    if (a.gx.tile_ptr) gather_rows<T, TX>(a.gx, tile_id, a.p, L, x0, z0, ax, TZ);
-    if (a.gz.tile_ptr) gather_rows<T, TX>(a.gz, tile_id, a.p, L, x0, z0, az, TZ);
+    const int64_t origin = L.base + z0 * L.px + x0;
+    if (a.gx.ptr) add_entries(a.gx, tile_id, (const T*)a.p, origin, ax, tid, 256);
+    if (a.gz.ptr) add_entries(a.gz, tile_id, (const T*)a.p, origin, az, tid, 256);
     __syncthreads();
     for (int i = tid; i < TZ * TX; i += 256) {
         int lz = i / TX, lx = i - lz * TX;
         int64_t x = x0 + lx, z = z0 + lz;
         if (x >= L.nx || z >= L.nz) continue;
-        int64_t q = L.base + z * L.px + x;
-        a.vx[q] += a.bx[q] * (ax[i] * a.inv_h);
-        a.vz[q] += a.bz[q] * (az[i] * a.inv_h);
+        int64_t q = origin + lz * L.px + lx;
+        a.vx[q] += a.bx[q] * ax[i];
+        a.vz[q] += a.bz[q] * az[i];
     }
 }
 
@@ -340,17 +378,17 @@ __global__ void __launch_bounds__(256) k_stag_p2d(StagArgs<T> a) {
     }
     __syncthreads();
     const int64_t tile_id = (int64_t)blockIdx.y * a.dx.ntx + blockIdx.x;
-    if (a.dx.tile_ptr) gather_rows<T, TX>(a.dx, tile_id, a.vx, L, x0, z0, acc, TZ);
-    __syncthreads();
-    if (a.dz.tile_ptr) gather_rows<T, TX>(a.dz, tile_id, a.vz, L, x0, z0, acc, TZ);
+    const int64_t origin = L.base + z0 * L.px + x0;
+    if (a.dx.ptr) add_entries(a.dx, tile_id, (const T*)a.vx, origin, acc, tid, 256);
+    if (a.dz.ptr) add_entries(a.dz, tile_id, (const T*)a.vz, origin, acc, tid, 256);
     __syncthreads();
     const T wv = a.src.n ? a.wavelet[a.step] : (T)0;
     for (int i = tid; i < TZ * TX; i += 256) {
         int lz = i / TX, lx = i - lz * TX;
         int64_t x = x0 + lx, z = z0 + lz;
         if (x >= L.nx || z >= L.nz) continue;
-        int64_t q = L.base + z * L.px + x;
-        T v = a.p[q] + a.kp[q] * (acc[i] * a.inv_h);
+        int64_t q = origin + lz * L.px + lx;
+        T v = a.p[q] + a.kp[q] * acc[i];
         for (int s = 0; s < 8 * a.src.n; ++s)
             if (a.src.idx[s] == q) v += a.src.w[s] * wv;
         a.p[q] = v;
@@ -370,12 +408,11 @@ struct AdjArgs {
     const T* mu;         // mu^{m+1}
     const T* mum;        // mu^{m+2}
     T* out;              // mu^m (may alias mum)
-    const T* K;
+    const T* Kh;         // dt^2 c^2 / h^2
     const uint8_t* mask;
-    T inv_h2;
-    T dt;
-    OpView<T> opT;       // transposed corrections (rows keyed by column node)
-    OpView<T> inj;       // receiver injection rows: w = interpolation weight, col_pad = receiver id
+    T two_dt_over_h;     // 2 dt / h  (2 / c = two_dt_over_h / sqrt(Kh))
+    TileView<T> opT;     // transposed corrections, keyed by column node
+    RowView<T> inj;      // receiver injection: col = receiver id
     const T* res;        // [nrec][nt]
     int nt;
     int m;
@@ -401,7 +438,7 @@ __global__ void __launch_bounds__(256) k_adj2d(AdjArgs<T> a) {
         T v = 0;
         if (x < L.nx + H && z < L.nz + H) {
             int64_t q = L.base + z * L.px + x;
-            v = a.K[q] * a.mu[q];
+            v = a.Kh[q] * a.mu[q];
         }
         tile[lz][lx] = v;
     }
@@ -413,29 +450,17 @@ __global__ void __launch_bounds__(256) k_adj2d(AdjArgs<T> a) {
 #pragma unroll
         for (int k = 1; k <= H; ++k)
             s += a.w2[k] * ((tile[lz + H][lx + H + k] + tile[lz + H][lx + H - k]) +
-                             (tile[lz + H + k][lx + H] + tile[lz + H - k][lx + H]));
-        acc[i] = s * a.inv_h2;
+                            (tile[lz + H + k][lx + H] + tile[lz + H - k][lx + H]));
+        acc[i] = s;
     }
     __syncthreads();
     const int64_t tile_id = (int64_t)blockIdx.y * a.opT.ntx + blockIdx.x;
-    // transposed IB corrections: sum_i w_ij K_i mu_i
-    if (a.opT.tile_ptr) {
-        const int warp = tid >> 5, lane = tid & 31;
-        for (int k = a.opT.tile_ptr[tile_id] + warp; k < a.opT.tile_ptr[tile_id + 1]; k += 8) {
-            const int32_t r = a.opT.perm[k];
-            const int64_t q = a.opT.row_pad[r];
-            T s = 0;
-            for (int64_t j = a.opT.row_ptr[r] + lane; j < a.opT.row_ptr[r + 1]; j += 32) {
-                int64_t src = q + a.opT.col_pad[j];
-                s += a.opT.w[j] * (a.K[src] * a.mu[src]);
-            }
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-            if (lane == 0) {
-                int64_t loc = q - L.base;
-                int64_t z = loc / L.px, x = loc - z * L.px;
-                acc[(z - z0) * TX + (x - x0)] += s * a.inv_h2;
-            }
+    const int64_t origin = L.base + z0 * L.px + x0;
+    if (a.opT.ptr) {
+        const int32_t e0 = a.opT.ptr[tile_id], e1 = a.opT.ptr[tile_id + 1];
+        for (int32_t e = e0 + tid; e < e1; e += 256) {
+            int64_t s = origin + a.opT.src[e];
+            atomicAdd(&acc[a.opT.loc[e]], a.opT.w[e] * (a.Kh[s] * a.mu[s]));
         }
     }
     __syncthreads();
@@ -443,11 +468,9 @@ __global__ void __launch_bounds__(256) k_adj2d(AdjArgs<T> a) {
         int lz = i / TX, lx = i - lz * TX;
         int64_t x = x0 + lx, z = z0 + lz;
         if (x >= L.nx || z >= L.nz) continue;
-        int64_t q = L.base + z * L.px + x;
-        acc[i] = a.mask[q] ? acc[i] : (T)0;
+        acc[i] = a.mask[origin + lz * L.px + lx] ? acc[i] : (T)0;
     }
     __syncthreads();
-    // receiver residual injection R^T res^{m-1}
     if (a.inj.tile_ptr) {
         const int warp = tid >> 5, lane = tid & 31;
         for (int k = a.inj.tile_ptr[tile_id] + warp; k < a.inj.tile_ptr[tile_id + 1]; k += 8) {
@@ -455,13 +478,13 @@ __global__ void __launch_bounds__(256) k_adj2d(AdjArgs<T> a) {
             const int64_t q = a.inj.row_pad[r];
             T s = 0;
             for (int64_t j = a.inj.row_ptr[r] + lane; j < a.inj.row_ptr[r + 1]; j += 32)
-                s += a.inj.w[j] * a.res[a.inj.col_pad[j] * (int64_t)a.nt + (a.m - 1)];
+                s += a.inj.w[j] * a.res[a.inj.col[j] * (int64_t)a.nt + (a.m - 1)];
 #pragma unroll
             for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
             if (lane == 0) {
-                int64_t loc = q - L.base;
-                int64_t z = loc / L.px, x = loc - z * L.px;
-                acc[(z - z0) * TX + (x - x0)] += s;
+                int64_t loc = q - origin;
+                int64_t dz = loc / L.px;
+                acc[dz * TX + (loc - dz * L.px)] += s;
             }
         }
     }
@@ -471,48 +494,48 @@ __global__ void __launch_bounds__(256) k_adj2d(AdjArgs<T> a) {
         int lz = i / TX, lx = i - lz * TX;
         int64_t x = x0 + lx, z = z0 + lz;
         if (x >= L.nx || z >= L.nz) continue;
-        int64_t q = L.base + z * L.px + x;
+        int64_t q = origin + lz * L.px + lx;
         T mu_new = (T)2 * a.mu[q] - a.mum[q] + acc[i];
         a.out[q] = mu_new;
-        T Kq = a.K[q];
+        T Kq = a.Kh[q];
         if (Kq > (T)0) {
-            T d2 = a.pm0[q] - (T)2 * a.pm1[q] + a.pm2[q];
+            T d2 = (a.pm0[q] - a.pm1[q]) - (a.pm1[q] - a.pm2[q]);
             T srcw = 0;
             for (int s = 0; s < 8 * a.src.n; ++s)
                 if (a.src.idx[s] == q) srcw += a.src.w[s];
             d2 -= srcw * wv;
-            a.grad[q] += mu_new * ((T)2 * a.dt / sqrt(Kq)) * d2;
+            a.grad[q] += mu_new * (a.two_dt_over_h / sqrt(Kq)) * d2;
             if (a.gw && srcw != (T)0) atomicAdd(&a.gw[a.m - 1], srcw * mu_new);
         }
     }
 }
 
 // ---------------------------------------------------------------------------
-// setup kernels
+// setup kernels (coefficients formed in FP64, rounded once)
 // ---------------------------------------------------------------------------
 template <typename T>
-__global__ void k_leap_coef(Layout L, const T* vel, const uint8_t* mask, T dt, T* K) {
+__global__ void k_leap_coef(Layout L, const T* vel, const uint8_t* mask, double dt_over_h, T* Kh) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < L.N; i += (int64_t)gridDim.x * blockDim.x) {
         int64_t x = i % L.nx, r = i / L.nx, y = r % L.ny, z = r / L.ny;
         int64_t q = L.idx(x, y, z);
-        T c = vel[i];
-        K[q] = mask[q] ? dt * dt * c * c : (T)0;
+        double c = (double)vel[i] * dt_over_h;
+        Kh[q] = mask[q] ? (T)(c * c) : (T)0;
     }
 }
 
 template <typename T>
 __global__ void k_stag_coef(Layout L, const T* vel, const T* rho, const uint8_t* mp, const uint8_t* mvx,
-                            const uint8_t* mvz, T dt, T* kp, T* bx, T* bz) {
+                            const uint8_t* mvz, double dt, double inv_h, T* kp, T* bx, T* bz) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < L.N; i += (int64_t)gridDim.x * blockDim.x) {
         int64_t x = i % L.nx, z = i / L.nx;
         int64_t q = L.idx(x, 0, z);
-        T r0 = rho ? rho[i] : (T)1;
-        T c = vel[i];
-        kp[q] = mp[q] ? dt * r0 * c * c : (T)0;
-        T rx = (rho && x + 1 < L.nx) ? rho[i + 1] : r0;
-        T rz = (rho && z + 1 < L.nz) ? rho[i + L.nx] : r0;
-        bx[q] = mvx[q] ? dt * (T)0.5 * ((T)1 / r0 + (T)1 / rx) : (T)0;
-        bz[q] = mvz[q] ? dt * (T)0.5 * ((T)1 / r0 + (T)1 / rz) : (T)0;
+        double r0 = rho ? (double)rho[i] : 1.0;
+        double c = (double)vel[i];
+        kp[q] = mp[q] ? (T)(dt * r0 * c * c * inv_h) : (T)0;
+        double rx = (rho && x + 1 < L.nx) ? (double)rho[i + 1] : r0;
+        double rz = (rho && z + 1 < L.nz) ? (double)rho[i + L.nx] : r0;
+        bx[q] = mvx[q] ? (T)(dt * 0.5 * (1.0 / r0 + 1.0 / rx) * inv_h) : (T)0;
+        bz[q] = mvz[q] ? (T)(dt * 0.5 * (1.0 / r0 + 1.0 / rz) * inv_h) : (T)0;
     }
 }
 
@@ -520,14 +543,13 @@ template <typename T>
 __global__ void k_interp_setup(int n, const double* xyz, int ndim, double inv_h, Layout L, const uint8_t* mask,
                                double scale, int64_t* idx, T* w) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-        double xi[3] = {0, 0, 0};
         int64_t b[3] = {0, 0, 0};
         double fr[3] = {0, 0, 0};
         int64_t nn[3] = {L.nx, ndim == 3 ? L.ny : L.nz, L.nz};
         for (int a = 0; a < ndim; ++a) {
-            xi[a] = xyz[(int64_t)i * ndim + a] * inv_h;
-            b[a] = (int64_t)floor(xi[a]);
-            fr[a] = xi[a] - (double)b[a];
+            double xi = xyz[(int64_t)i * ndim + a] * inv_h;
+            b[a] = (int64_t)floor(xi);
+            fr[a] = xi - (double)b[a];
         }
         for (int c = 0; c < 8; ++c) {
             double wt = 0.0;
@@ -547,7 +569,6 @@ __global__ void k_interp_setup(int n, const double* xyz, int ndim, double inv_h,
                     if (mask && !mask[q]) wt = 0.0;
                 } else {
                     wt = 0.0;
-                    q = L.base;
                 }
                 if (wt == 0.0) q = L.base;
             }
@@ -601,40 +622,22 @@ static void stencil_weights(int M, T w2o[5], T c1o[4]) {
 }
 
 template <typename T>
-static OpView<T> view_of(const IbOp& o, const TileBins* b, const Layout& L) {
-    OpView<T> v;
+static TileView<T> tview(const TileBins* b) {
+    TileView<T> v;
     memset(&v, 0, sizeof v);
-    if (!b || o.nrows == 0) return v;
-    v.row_pad = o.row_pad;
-    v.row_ptr = o.row_ptr;
-    v.col_pad = o.col_pad;
-    v.w = (const T*)(sizeof(T) == 8 ? (const void*)o.w64 : (const void*)o.w32);
-    v.tile_ptr = b->tile_ptr;
-    v.perm = b->perm;
-    v.ntx = (L.nx + b->tx - 1) / b->tx;
-    v.nty = (L.ndim == 3 ? (L.ny + b->ty - 1) / b->ty : 1);
-    return v;
-}
-
-template <typename T>
-static OpView<T> view_of_t(const IbOp& o, const TileBins* b, const Layout& L) {
-    OpView<T> v;
-    memset(&v, 0, sizeof v);
-    if (!b || o.t_nrows == 0) return v;
-    v.row_pad = o.t_row_pad;
-    v.row_ptr = o.t_ptr;
-    v.col_pad = o.t_src_off;
-    v.w = (const T*)(sizeof(T) == 8 ? (const void*)o.t_w64 : (const void*)o.t_w32);
-    v.tile_ptr = b->tile_ptr;
-    v.perm = b->perm;
-    v.ntx = (L.nx + b->tx - 1) / b->tx;
-    v.nty = 1;
+    if (!b || b->nent == 0) return v;
+    v.ptr = b->ent_ptr;
+    v.loc = b->ent_loc;
+    v.src = b->ent_src;
+    v.w = (const T*)(sizeof(T) == 8 ? (const void*)b->ent_w64 : (const void*)b->ent_w32);
+    v.ntx = b->ntx;
     return v;
 }
 
 static const int TX2 = 64, TZ2 = 8;
 
-static ib_status check_shot(const ib_table* t, const ib_shot* sh, int precision, double dt, int nt) {
+static ib_status check_shot(const ib_table* t, const ib_shot* sh, int precision, double dt, int nt,
+                            bool need_traces = true) {
     if (!t || !sh) {
         ib_set_error("null table or shot");
         return IB_ERR_ARG;
@@ -648,7 +651,7 @@ static ib_status check_shot(const ib_table* t, const ib_shot* sh, int precision,
         return IB_ERR_ARG;
     }
     if (!sh->vel_dev || sh->nsrc < 0 || sh->nrec < 0 || (sh->nsrc && (!sh->src_dev || !sh->wavelet_dev)) ||
-        (sh->nrec && (!sh->rec_dev || !sh->traces_dev))) {
+        (sh->nrec && (!sh->rec_dev || (need_traces && !sh->traces_dev)))) {
         ib_set_error("missing shot arrays");
         return IB_ERR_ARG;
     }
@@ -676,14 +679,17 @@ static ib_status setup_points(const ib_table* t, const ib_shot* sh, double scale
     TRY(S.alloc(&sw, 8 * std::max(sh->nsrc, 1)));
     TRY(S.alloc(&ri, 8 * std::max(sh->nrec, 1)));
     TRY(S.alloc(&rw, 8 * std::max(sh->nrec, 1)));
-    if (sh->nsrc)
+    if (sh->nsrc) {
         k_interp_setup<T><<<grid1(sh->nsrc, 64), 64, 0, S.s>>>(sh->nsrc, sh->src_dev, d, 1.0 / t->grid.h, L,
                                                                 t->mask_pad[0], scale, si, sw);
-    if (sh->nrec)
+        ib_count_launch("setup");
+    }
+    if (sh->nrec) {
         k_interp_setup<T><<<grid1(sh->nrec, 64), 64, 0, S.s>>>(sh->nrec, sh->rec_dev, d, 1.0 / t->grid.h, L,
                                                                 t->mask_pad[0], 1.0, ri, rw);
+        ib_count_launch("setup");
+    }
     IB_CHECK_LAUNCH("k_interp_setup");
-    ib_count_launch("setup");
     g.src = {sh->nsrc, si, sw};
     g.rec = {sh->nrec, ri, rw};
     return IB_OK;
@@ -699,6 +705,16 @@ extern "C" int64_t ib_checkpoint_bytes(const ib_table* t, int32_t precision, int
 }
 
 template <typename T>
+static void launch_leap2d(const StepArgs<T>& a, int H, dim3 grid, cudaStream_t s) {
+    PROF_LAUNCH(kname<T>("leap2d_f32", "leap2d_f64"), s, {
+        if (H == 1) k_leap2d<T, 1, TX2, TZ2><<<grid, 256, 0, s>>>(a);
+        else if (H == 2) k_leap2d<T, 2, TX2, TZ2><<<grid, 256, 0, s>>>(a);
+        else if (H == 3) k_leap2d<T, 3, TX2, TZ2><<<grid, 256, 0, s>>>(a);
+        else k_leap2d<T, 4, TX2, TZ2><<<grid, 256, 0, s>>>(a);
+    });
+}
+
+template <typename T>
 static ib_status forward_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, void* ckpt, int n_ckpt,
                              cudaStream_t s) {
     const Layout& L = t->L;
@@ -706,22 +722,18 @@ static ib_status forward_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, 
     const int M = t->opts.space_order;
     const int H = M / 2;
     Scratch S(s);
-    T *p0, *p1, *K;
+    T *p0, *p1, *Kh;
     TRY(S.alloc(&p0, L.total, true));
     TRY(S.alloc(&p1, L.total, true));
-    TRY(S.alloc(&K, L.total, true));
-    k_leap_coef<T><<<grid1(L.N, 256), 256, 0, s>>>(L, (const T*)sh->vel_dev, t->mask_pad[0], (T)dt, K);
+    TRY(S.alloc(&Kh, L.total, true));
+    k_leap_coef<T><<<grid1(L.N, 256), 256, 0, s>>>(L, (const T*)sh->vel_dev, t->mask_pad[0], dt / t->grid.h, Kh);
     IB_CHECK_LAUNCH("k_leap_coef");
     ib_count_launch("setup");
     Geom<T> g;
     TRY(setup_points<T>(t, sh, dt * dt / pow(t->grid.h, d), S, g));
     const TileBins* bins = nullptr;
-    int tx = d == 2 ? TX2 : 32, ty = d == 2 ? 1 : 8, tz = d == 2 ? TZ2 : 1;
     if (d == 2) TRY(ib_table_bins(t, 0, false, TX2, 1, TZ2, &bins, s));
     else TRY(ib_table_bins(t, 0, false, 32, 8, 1, &bins, s));
-    (void)tx;
-    (void)ty;
-    (void)tz;
     StepArgs<T> a;
     memset(&a, 0, sizeof a);
     a.L = L;
@@ -729,9 +741,8 @@ static ib_status forward_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, 
         T c1u[4];
         stencil_weights<T>(M, a.w2, c1u);
     }
-    a.K = K;
-    a.inv_h2 = (T)(1.0 / (t->grid.h * t->grid.h));
-    a.op = view_of<T>(t->ops[0], bins, L);
+    a.Kh = Kh;
+    a.op = tview<T>(bins);
     a.src = g.src;
     a.wavelet = (const T*)sh->wavelet_dev;
     a.rec = g.rec;
@@ -743,6 +754,7 @@ static ib_status forward_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, 
     dim3 grid2((unsigned)((L.nx + TX2 - 1) / TX2), (unsigned)((L.nz + TZ2 - 1) / TZ2));
     const int zchunk = 32;
     dim3 grid3((unsigned)((L.nx + 31) / 32), (unsigned)((L.ny + 7) / 8), (unsigned)((L.nz + zchunk - 1) / zchunk));
+    const int64_t nty3 = (L.ny + 7) / 8;
     for (int n = 0; n < nt; ++n) {
         if (ckpt && n % seg == 0) {
             T* slot = (T*)ckpt + (int64_t)(n / seg) * 2 * L.total;
@@ -755,28 +767,24 @@ static ib_status forward_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, 
         a.step = n;
         a.rec_step = n - 1;
         if (d == 2) {
-            PROF_LAUNCH(kname<T>("leap2d_f32", "leap2d_f64"), s, {
-                if (H == 1) k_leap2d<T, 1, TX2, TZ2><<<grid2, 256, 0, s>>>(a);
-                else if (H == 2) k_leap2d<T, 2, TX2, TZ2><<<grid2, 256, 0, s>>>(a);
-                else if (H == 3) k_leap2d<T, 3, TX2, TZ2><<<grid2, 256, 0, s>>>(a);
-                else k_leap2d<T, 4, TX2, TZ2><<<grid2, 256, 0, s>>>(a);
-            });
+            launch_leap2d<T>(a, H, grid2, s);
         } else {
             dim3 blk(32, 8);
             PROF_LAUNCH(kname<T>("leap3d_f32", "leap3d_f64"), s, {
-                if (H == 1) k_leap3d<T, 1><<<grid3, blk, 0, s>>>(a, zchunk);
-                else if (H == 2) k_leap3d<T, 2><<<grid3, blk, 0, s>>>(a, zchunk);
-                else if (H == 3) k_leap3d<T, 3><<<grid3, blk, 0, s>>>(a, zchunk);
-                else k_leap3d<T, 4><<<grid3, blk, 0, s>>>(a, zchunk);
+                if (H == 1) k_leap3d<T, 1><<<grid3, blk, 0, s>>>(a, zchunk, nty3);
+                else if (H == 2) k_leap3d<T, 2><<<grid3, blk, 0, s>>>(a, zchunk, nty3);
+                else if (H == 3) k_leap3d<T, 3><<<grid3, blk, 0, s>>>(a, zchunk, nty3);
+                else k_leap3d<T, 4><<<grid3, blk, 0, s>>>(a, zchunk, nty3);
             });
         }
         IB_CHECK_LAUNCH("leapfrog step");
         std::swap(cur, prev);
     }
-    if (g.rec.n)
+    if (g.rec.n) {
         k_receivers<T><<<grid1(g.rec.n, 256), 256, 0, s>>>(g.rec, cur, (T*)sh->traces_dev, nt, nt - 1);
-    IB_CHECK_LAUNCH("k_receivers");
-    ib_count_launch("setup");
+        IB_CHECK_LAUNCH("k_receivers");
+        ib_count_launch("setup");
+    }
     return IB_OK;
 }
 
@@ -799,7 +807,7 @@ static ib_status forward_stag(ib_table* t, const ib_shot* sh, double dt, int nt,
     TRY(S.alloc(&bx, L.total, true));
     TRY(S.alloc(&bz, L.total, true));
     k_stag_coef<T><<<grid1(L.N, 256), 256, 0, s>>>(L, (const T*)sh->vel_dev, (const T*)sh->rho_dev, t->mask_pad[0],
-                                                   t->mask_pad[1], t->mask_pad[2], (T)dt, kp, bx, bz);
+                                                   t->mask_pad[1], t->mask_pad[2], dt, 1.0 / t->grid.h, kp, bx, bz);
     IB_CHECK_LAUNCH("k_stag_coef");
     ib_count_launch("setup");
     Geom<T> g;
@@ -819,11 +827,13 @@ static ib_status forward_stag(ib_table* t, const ib_shot* sh, double dt, int nt,
     a.bx = bx;
     a.bz = bz;
     a.kp = kp;
-    a.inv_h = (T)(1.0 / t->grid.h);
-    a.gx = view_of<T>(t->ops[0], b[0], L);
-    a.gz = view_of<T>(t->ops[1], b[1], L);
-    a.dx = view_of<T>(t->ops[2], b[2], L);
-    a.dz = view_of<T>(t->ops[3], b[3], L);
+    a.gx = tview<T>(b[0]);
+    a.gz = tview<T>(b[1]);
+    a.dx = tview<T>(b[2]);
+    a.dz = tview<T>(b[3]);
+    // the four views share one tile grid: give every view the grid's width
+    int64_t ntx = (L.nx + TX2 - 1) / TX2;
+    a.gx.ntx = a.gz.ntx = a.dx.ntx = a.dz.ntx = ntx;
     a.src = g.src;
     a.wavelet = (const T*)sh->wavelet_dev;
     a.rec = g.rec;
@@ -847,9 +857,11 @@ static ib_status forward_stag(ib_table* t, const ib_shot* sh, double dt, int nt,
         });
         IB_CHECK_LAUNCH("staggered step");
     }
-    if (g.rec.n) k_receivers<T><<<grid1(g.rec.n, 256), 256, 0, s>>>(g.rec, p, (T*)sh->traces_dev, nt, nt - 1);
-    IB_CHECK_LAUNCH("k_receivers");
-    ib_count_launch("setup");
+    if (g.rec.n) {
+        k_receivers<T><<<grid1(g.rec.n, 256), 256, 0, s>>>(g.rec, p, (T*)sh->traces_dev, nt, nt - 1);
+        IB_CHECK_LAUNCH("k_receivers");
+        ib_count_launch("setup");
+    }
     return IB_OK;
 }
 
@@ -874,15 +886,9 @@ extern "C" ib_status ib_forward(const ib_table* tc, const ib_shot* sh, int32_t p
     return precision == 64 ? forward_stag<double>(t, sh, dt, nt, s) : forward_stag<float>(t, sh, dt, nt, s);
 }
 
-// receiver injection table: node -> (receiver, weight), built on the host from the corner lists
+// receiver injection rows: node -> (receiver, weight), regrouped on the host
 template <typename T>
-struct InjTable {
-    IbOp op;      // row_pad, row_ptr, col_pad = receiver id, w32/w64
-    TileBins* bins = nullptr;
-};
-
-template <typename T>
-static ib_status build_injection(const Layout& L, const PointSet<T>& rec, Scratch& S, OpView<T>& view,
+static ib_status build_injection(const Layout& L, const PointSet<T>& rec, Scratch& S, RowView<T>& view,
                                  std::vector<TileBins>& keep) {
     memset(&view, 0, sizeof view);
     if (rec.n == 0) return IB_OK;
@@ -928,12 +934,11 @@ static ib_status build_injection(const Layout& L, const PointSet<T>& rec, Scratc
     keep.push_back(b);
     view.row_pad = drows;
     view.row_ptr = dptr;
-    view.col_pad = dcol;
+    view.col = dcol;
     view.w = dw;
     view.tile_ptr = b.tile_ptr;
     view.perm = b.perm;
-    view.ntx = (L.nx + TX2 - 1) / TX2;
-    view.nty = 1;
+    view.ntx = b.ntx;
     IB_CUDA(cudaStreamSynchronize(S.s));
     return IB_OK;
 }
@@ -949,14 +954,13 @@ static ib_status adjoint_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, 
     }
     const int M = t->opts.space_order;
     const int H = M / 2;
-    TRY(ib_table_transpose(t, 0, s));
     Scratch S(s);
-    T *K, *mu1, *mu2, *grad;
-    TRY(S.alloc(&K, L.total, true));
+    T *Kh, *mu1, *mu2, *grad;
+    TRY(S.alloc(&Kh, L.total, true));
     TRY(S.alloc(&mu1, L.total, true));
     TRY(S.alloc(&mu2, L.total, true));
     TRY(S.alloc(&grad, L.total, true));
-    k_leap_coef<T><<<grid1(L.N, 256), 256, 0, s>>>(L, (const T*)sh->vel_dev, t->mask_pad[0], (T)dt, K);
+    k_leap_coef<T><<<grid1(L.N, 256), 256, 0, s>>>(L, (const T*)sh->vel_dev, t->mask_pad[0], dt / t->grid.h, Kh);
     IB_CHECK_LAUNCH("k_leap_coef");
     ib_count_launch("setup");
     Geom<T> g;
@@ -966,7 +970,7 @@ static ib_status adjoint_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, 
     TRY(ib_table_bins(t, 0, false, TX2, 1, TZ2, &fb, s));
     TRY(ib_table_bins(t, 0, true, TX2, 1, TZ2, &tb, s));
     std::vector<TileBins> keep;
-    OpView<T> inj;
+    RowView<T> inj;
     TRY(build_injection<T>(L, g.rec, S, inj, keep));
     const int64_t seg = ckpt_seg(nt, n_ckpt);
     T* segbuf;
@@ -979,9 +983,8 @@ static ib_status adjoint_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, 
         T c1u[4];
         stencil_weights<T>(M, fa.w2, c1u);
     }
-    fa.K = K;
-    fa.inv_h2 = (T)(1.0 / (t->grid.h * t->grid.h));
-    fa.op = view_of<T>(t->ops[0], fb, L);
+    fa.Kh = Kh;
+    fa.op = tview<T>(fb);
     fa.src = g.src;
     fa.wavelet = (const T*)sh->wavelet_dev;
     fa.rec.n = 0;
@@ -991,12 +994,13 @@ static ib_status adjoint_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, 
     memset(&aa, 0, sizeof aa);
     aa.L = L;
     for (int k = 0; k < 5; ++k) aa.w2[k] = fa.w2[k];
-    aa.K = K;
+    aa.Kh = Kh;
     aa.mask = t->mask_pad[0];
-    aa.inv_h2 = fa.inv_h2;
-    aa.dt = (T)dt;
-    aa.opT = view_of_t<T>(t->ops[0], tb, L);
+    aa.two_dt_over_h = (T)(2.0 * dt / t->grid.h);
+    aa.opT = tview<T>(tb);
+    aa.opT.ntx = (L.nx + TX2 - 1) / TX2;
     aa.inj = inj;
+    aa.inj.ntx = aa.opT.ntx;
     aa.res = res;
     aa.nt = nt;
     aa.grad = grad;
@@ -1019,12 +1023,7 @@ static ib_status adjoint_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, 
             fa.pm = segbuf + (n - c) * L.total;
             fa.out = segbuf + (n - c + 2) * L.total;
             fa.step = (int)n;
-            PROF_LAUNCH(kname<T>("leap2d_f32", "leap2d_f64"), s, {
-                if (H == 1) k_leap2d<T, 1, TX2, TZ2><<<grid2, 256, 0, s>>>(fa);
-                else if (H == 2) k_leap2d<T, 2, TX2, TZ2><<<grid2, 256, 0, s>>>(fa);
-                else if (H == 3) k_leap2d<T, 3, TX2, TZ2><<<grid2, 256, 0, s>>>(fa);
-                else k_leap2d<T, 4, TX2, TZ2><<<grid2, 256, 0, s>>>(fa);
-            });
+            launch_leap2d<T>(fa, H, grid2, s);
             IB_CHECK_LAUNCH("recompute step");
         }
         for (int64_t m = e; m >= c + 1; --m) {
@@ -1049,10 +1048,7 @@ static ib_status adjoint_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, 
     IB_CHECK_LAUNCH("k_unpad");
     ib_count_launch("setup");
     IB_CUDA(cudaStreamSynchronize(s));
-    for (auto& b : keep) {
-        cudaFree(b.tile_ptr);
-        cudaFree(b.perm);
-    }
+    for (auto& b : keep) ib_free_bins(b);
     return IB_OK;
 }
 
@@ -1060,7 +1056,7 @@ extern "C" ib_status ib_adjoint(const ib_table* tc, const ib_shot* sh, int32_t p
                                 const void* ckpt, int32_t n_ckpt, const void* residual, void* grad_vel,
                                 void* grad_wavelet, void* stream) {
     ib_set_error("");
-    TRY(check_shot(tc, sh, precision, dt, nt));
+    TRY(check_shot(tc, sh, precision, dt, nt, false));
     if (!ckpt || n_ckpt < 1 || !residual || !grad_vel) {
         ib_set_error("adjoint needs checkpoints, residual and gradient buffers");
         return IB_ERR_ARG;
@@ -1078,6 +1074,95 @@ extern "C" ib_status ib_adjoint(const ib_table* tc, const ib_shot* sh, int32_t p
                               (float*)grad_wavelet, s);
 }
 
+// ---------------------------------------------------------------------------
+// batched shots: one launch per time step over the tiles of every shot,
+// captured with all nt steps into one CUDA graph; the tile shape is chosen by
+// timing the candidates on the batch itself (cached per shape class)
+// ---------------------------------------------------------------------------
+struct TileShape {
+    int tx, tz;
+};
+static const TileShape kShapes[4] = {{64, 8}, {32, 16}, {128, 4}, {64, 4}};
+
+template <int H, int TX, int TZ>
+static void launch_batch(const StepArgs<float>* args, const int64_t* tile0, int nshot, int step, int64_t nblk,
+                         cudaStream_t s) {
+    k_leap2d_batch<float, H, TX, TZ><<<(unsigned)nblk, 256, 0, s>>>(args, tile0, nshot, step);
+}
+
+template <int H>
+static void launch_batch_shape(int si, const StepArgs<float>* args, const int64_t* tile0, int nshot, int step,
+                               int64_t nblk, cudaStream_t s) {
+    switch (si) {
+        case 0: launch_batch<H, 64, 8>(args, tile0, nshot, step, nblk, s); break;
+        case 1: launch_batch<H, 32, 16>(args, tile0, nshot, step, nblk, s); break;
+        case 2: launch_batch<H, 128, 4>(args, tile0, nshot, step, nblk, s); break;
+        default: launch_batch<H, 64, 4>(args, tile0, nshot, step, nblk, s); break;
+    }
+}
+
+static void launch_batch_any(int H, int si, const StepArgs<float>* args, const int64_t* tile0, int nshot, int step,
+                             int64_t nblk, cudaStream_t s) {
+    PROF_LAUNCH("leap2d_batch_f32", s, {
+        if (H == 1) launch_batch_shape<1>(si, args, tile0, nshot, step, nblk, s);
+        else if (H == 2) launch_batch_shape<2>(si, args, tile0, nshot, step, nblk, s);
+        else if (H == 3) launch_batch_shape<3>(si, args, tile0, nshot, step, nblk, s);
+        else launch_batch_shape<4>(si, args, tile0, nshot, step, nblk, s);
+    });
+}
+
+static std::mutex g_tune_mu;
+static std::map<std::pair<int, int64_t>, int> g_tuned;   // (H, total points / 2^18) -> shape index
+
+struct BatchSetup {
+    std::vector<StepArgs<float>> args;
+    std::vector<int64_t> tile0;
+    StepArgs<float>* d_args = nullptr;
+    int64_t* d_tile0 = nullptr;
+    int64_t nblk = 0;
+};
+
+static ib_status batch_prepare(ib_table* const* ts, const ib_shot* shots, int nshot, int si, double dt, int nt,
+                               const std::vector<float*>& buf0, const std::vector<float*>& buf1,
+                               const std::vector<float*>& Kh, const std::vector<Geom<float>>& geo, Scratch& S,
+                               BatchSetup& B) {
+    const int tx = kShapes[si].tx, tz = kShapes[si].tz;
+    B.args.assign(nshot, StepArgs<float>());
+    B.tile0.assign(nshot + 1, 0);
+    for (int i = 0; i < nshot; ++i) {
+        ib_table* t = ts[i];
+        const Layout& L = t->L;
+        const TileBins* bins = nullptr;
+        TRY(ib_table_bins(t, 0, false, tx, 1, tz, &bins, S.s));
+        StepArgs<float>& a = B.args[i];
+        memset(&a, 0, sizeof a);
+        a.L = L;
+        float c1u[4];
+        stencil_weights<float>(t->opts.space_order, a.w2, c1u);
+        a.Kh = Kh[i];
+        a.op = tview<float>(bins);
+        a.src = geo[i].src;
+        a.wavelet = (const float*)shots[i].wavelet_dev;
+        a.rec = geo[i].rec;
+        a.traces = (float*)shots[i].traces_dev;
+        a.nt = nt;
+        a.buf0 = buf0[i];
+        a.buf1 = buf1[i];
+        a.ntx = (L.nx + tx - 1) / tx;
+        int64_t ntiles = a.ntx * ((L.nz + tz - 1) / tz);
+        a.ntiles = ntiles;
+        // receivers are recorded by the first blocks of the shot: make sure there are enough
+        int64_t need = (shots[i].nrec + 255) / 256;
+        B.tile0[i + 1] = B.tile0[i] + std::max(ntiles, need);
+    }
+    B.nblk = B.tile0[nshot];
+    TRY(S.alloc(&B.d_args, nshot));
+    TRY(S.alloc(&B.d_tile0, nshot + 1));
+    IB_CUDA(cudaMemcpyAsync(B.d_args, B.args.data(), sizeof(StepArgs<float>) * nshot, cudaMemcpyHostToDevice, S.s));
+    IB_CUDA(cudaMemcpyAsync(B.d_tile0, B.tile0.data(), 8 * (nshot + 1), cudaMemcpyHostToDevice, S.s));
+    return IB_OK;
+}
+
 extern "C" ib_status ib_forward_batch(const ib_table* const* tables, const ib_shot* shots, int32_t nshot,
                                       int32_t precision, double dt, int32_t nt, void* stream) {
     ib_set_error("");
@@ -1085,7 +1170,134 @@ extern "C" ib_status ib_forward_batch(const ib_table* const* tables, const ib_sh
         ib_set_error("empty batch");
         return IB_ERR_ARG;
     }
-    for (int i = 0; i < nshot; ++i) TRY(ib_forward(tables[i], &shots[i], precision, dt, nt, nullptr, 0, stream));
+    if (precision != 32) {
+        ib_set_error("batched shots run in FP32");
+        return IB_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<ib_table*> ts(nshot);
+    int H = -1;
+    for (int i = 0; i < nshot; ++i) {
+        TRY(check_shot(tables[i], &shots[i], precision, dt, nt));
+        ts[i] = const_cast<ib_table*>(tables[i]);
+        if (ts[i]->form != IB_SECOND_ORDER || ts[i]->grid.ndim != 2) {
+            ib_set_error("batched shots: 2D second-order tables only");
+            return IB_ERR_STATE;
+        }
+        int h = ts[i]->opts.space_order / 2;
+        if (H >= 0 && h != H) {
+            ib_set_error("batched shots must share the space order");
+            return IB_ERR_ARG;
+        }
+        H = h;
+    }
+    Scratch S(s);
+    std::vector<float*> b0(nshot), b1(nshot), Kh(nshot);
+    std::vector<Geom<float>> geo(nshot);
+    int64_t total = 0;
+    for (int i = 0; i < nshot; ++i) {
+        const Layout& L = ts[i]->L;
+        TRY(S.alloc(&b0[i], L.total, true));
+        TRY(S.alloc(&b1[i], L.total, true));
+        TRY(S.alloc(&Kh[i], L.total, true));
+        k_leap_coef<float><<<grid1(L.N, 256), 256, 0, s>>>(L, (const float*)shots[i].vel_dev, ts[i]->mask_pad[0],
+                                                           dt / ts[i]->grid.h, Kh[i]);
+        IB_CHECK_LAUNCH("k_leap_coef");
+        ib_count_launch("setup");
+        TRY(setup_points<float>(ts[i], &shots[i], dt * dt / pow(ts[i]->grid.h, 2), S, geo[i]));
+        total += L.N;
+    }
+    // ---- tile-shape autotuning (first batch of a shape class)
+    int best = 0;
+    {
+        std::pair<int, int64_t> key(H, total >> 18);
+        bool have = false;
+        {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            auto it = g_tuned.find(key);
+            if (it != g_tuned.end()) {
+                best = it->second;
+                have = true;
+            }
+        }
+        if (!have) {
+            float best_ms = 1e30f;
+            cudaEvent_t e0, e1;
+            IB_CUDA(cudaEventCreate(&e0));
+            IB_CUDA(cudaEventCreate(&e1));
+            for (int si = 0; si < 4; ++si) {
+                BatchSetup B;
+                TRY(batch_prepare(ts.data(), shots, nshot, si, dt, nt, b0, b1, Kh, geo, S, B));
+                const int trial = std::min(nt, 12);
+                for (int n = 0; n < 2; ++n) launch_batch_any(H, si, B.d_args, B.d_tile0, nshot, n, B.nblk, s);
+                IB_CUDA(cudaEventRecord(e0, s));
+                for (int n = 0; n < trial; ++n) launch_batch_any(H, si, B.d_args, B.d_tile0, nshot, n, B.nblk, s);
+                IB_CUDA(cudaEventRecord(e1, s));
+                IB_CUDA(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                IB_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = si;
+                }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tuned[key] = best;
+            // trial steps wrote the wavefields: start the real run from zero
+            for (int i = 0; i < nshot; ++i) {
+                IB_CUDA(cudaMemsetAsync(b0[i], 0, sizeof(float) * ts[i]->L.total, s));
+                IB_CUDA(cudaMemsetAsync(b1[i], 0, sizeof(float) * ts[i]->L.total, s));
+            }
+        }
+    }
+    BatchSetup B;
+    TRY(batch_prepare(ts.data(), shots, nshot, best, dt, nt, b0, b1, Kh, geo, S, B));
+    // ---- all nt steps as one captured graph
+    cudaStream_t cs;
+    IB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaEvent_t ready;
+    IB_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    IB_CUDA(cudaEventRecord(ready, s));
+    IB_CUDA(cudaStreamWaitEvent(cs, ready, 0));
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    IB_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    for (int n = 0; n < nt; ++n) {
+        StepArgs<float>* dargs = B.d_args;
+        switch (H) {
+            case 1: launch_batch_shape<1>(best, dargs, B.d_tile0, nshot, n, B.nblk, cs); break;
+            case 2: launch_batch_shape<2>(best, dargs, B.d_tile0, nshot, n, B.nblk, cs); break;
+            case 3: launch_batch_shape<3>(best, dargs, B.d_tile0, nshot, n, B.nblk, cs); break;
+            default: launch_batch_shape<4>(best, dargs, B.d_tile0, nshot, n, B.nblk, cs); break;
+        }
+    }
+    cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+    if (ce != cudaSuccess) return ib_cuda_fail(ce, "graph capture", __FILE__, __LINE__);
+    IB_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+    {
+        ProfToken tk = ib_prof_begin("leap2d_batch_graph_f32", cs);
+        IB_CUDA(cudaGraphLaunch(exec, cs));
+        ib_prof_end(tk, cs);
+        for (int n = 0; n < nt; ++n) ib_count_launch("leap2d_batch_f32");
+    }
+    // final receivers per shot
+    for (int i = 0; i < nshot; ++i) {
+        if (!geo[i].rec.n) continue;
+        float* cur = (nt & 1) ? b1[i] : b0[i];
+        k_receivers<float><<<grid1(geo[i].rec.n, 256), 256, 0, cs>>>(geo[i].rec, cur, (float*)shots[i].traces_dev,
+                                                                      nt, nt - 1);
+        ib_count_launch("setup");
+    }
+    IB_CHECK_LAUNCH("k_receivers");
+    IB_CUDA(cudaEventRecord(ready, cs));
+    IB_CUDA(cudaStreamWaitEvent(s, ready, 0));
+    IB_CUDA(cudaStreamSynchronize(cs));
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    cudaEventDestroy(ready);
+    cudaStreamDestroy(cs);
     return IB_OK;
 }
 

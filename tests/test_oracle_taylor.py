@@ -192,6 +192,12 @@ def test_vector_bc_rows_vs_sympy(bc):
             exprs.append(sum(float(n) * sympy.diff(f, s) for n, s in zip(nrm, syms)))
             f = lap(f)
             k += 1
+        f = sympy.diff(v[1], syms[0]) - sympy.diff(v[0], syms[1])      # 2D curl
+        k = 0
+        while 2 * k + 1 <= M:
+            exprs.append(f)
+            f = lap(f)
+            k += 1
     rows = taylor.bc_rows_vector(bc, d, M, nrm)
     assert len(rows) == len(exprs)
     sub = dict(zip(syms, xb))
