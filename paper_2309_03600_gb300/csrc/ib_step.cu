@@ -91,6 +91,19 @@ __device__ __forceinline__ void add_entries(const TileView<T>& v, int64_t tile, 
     for (int32_t e = e0 + tid; e < e1; e += nthr) atomicAdd(&acc[v.loc[e]], v.w[e] * f[origin + v.src[e]]);
 }
 
+// source terms landing in a 2D tile (or one plane of a 3D tile): sadd[local] += w * wavelet
+template <typename T, int TXA, int TYA>
+__device__ __forceinline__ void tile_sources(const PointSet<T>& src, T wv, int64_t origin, int64_t px, T* sadd,
+                                             int tid) {
+    if (tid < 8 * src.n) {
+        const int64_t rel = src.idx[tid] - origin;
+        if (rel >= 0) {
+            const int64_t ly = rel / px, lx = rel - ly * px;
+            if (ly < TYA && lx < TXA && src.w[tid] != (T)0) atomicAdd(&sadd[ly * TXA + lx], src.w[tid] * wv);
+        }
+    }
+}
+
 template <typename T>
 __device__ __forceinline__ void record_receivers(const PointSet<T>& rec, const T* p, T* traces, int nt, int col,
                                                  int64_t gid) {
@@ -130,8 +143,9 @@ struct StepArgs {
 
 template <typename T, int H, int TX, int TZ>
 __device__ __forceinline__ void leap2d_tile(const StepArgs<T>& a, int64_t bx, int64_t bz, T (*tile)[TX + 2 * H],
-                                            T* acc) {
+                                            T* acc, T* sadd) {
     const int tid = threadIdx.x;
+    for (int i = tid; i < TZ * TX; i += 256) sadd[i] = (T)0;
     const int64_t x0 = bx * TX, z0 = bz * TZ;
     const Layout& L = a.L;
     for (int i = tid; i < (TZ + 2 * H) * (TX + 2 * H); i += 256) {
@@ -142,31 +156,31 @@ __device__ __forceinline__ void leap2d_tile(const StepArgs<T>& a, int64_t bx, in
         tile[lz][lx] = v;
     }
     __syncthreads();
+    // Laplacian in difference form, sum_k w_k sum_axes (p_{+k} - p_0 + p_{-k} - p_0): the
+    // discrete operator annihilates constants exactly in floating point (row sum zero)
     for (int i = tid; i < TZ * TX; i += 256) {
         int lz = i / TX, lx = i - lz * TX;
         T c = tile[lz + H][lx + H];
-        T s = (T)2 * a.w2[0] * c;
+        T s = 0;
 #pragma unroll
         for (int k = 1; k <= H; ++k)
-            s += a.w2[k] * ((tile[lz + H][lx + H + k] + tile[lz + H][lx + H - k]) +
-                            (tile[lz + H + k][lx + H] + tile[lz + H - k][lx + H]));
+            s += a.w2[k] * (((tile[lz + H][lx + H + k] - c) + (tile[lz + H][lx + H - k] - c)) +
+                            ((tile[lz + H + k][lx + H] - c) + (tile[lz + H - k][lx + H] - c)));
         acc[i] = s;
     }
-    __syncthreads();
     const int64_t origin = L.base + z0 * L.px + x0;
+    const T wv = a.src.n ? a.wavelet[a.step] : (T)0;
+    tile_sources<T, TX, TZ>(a.src, wv, origin, L.px, sadd, tid);
+    __syncthreads();
     if (a.op.ptr) add_entries(a.op, bz * a.op.ntx + bx, a.p, origin, acc, tid, 256);
     __syncthreads();
-    const T wv = a.src.n ? a.wavelet[a.step] : (T)0;
     for (int i = tid; i < TZ * TX; i += 256) {
         int lz = i / TX, lx = i - lz * TX;
         int64_t x = x0 + lx, z = z0 + lz;
         if (x >= L.nx || z >= L.nz) continue;
         int64_t q = origin + lz * L.px + lx;
         T c = tile[lz + H][lx + H];
-        T v = c + ((c - a.pm[q]) + a.Kh[q] * acc[i]);
-        for (int s = 0; s < 8 * a.src.n; ++s)
-            if (a.src.idx[s] == q) v += a.src.w[s] * wv;
-        a.out[q] = v;
+        a.out[q] = c + ((c - a.pm[q]) + a.Kh[q] * acc[i]) + sadd[i];
     }
 }
 
@@ -174,9 +188,10 @@ template <typename T, int H, int TX, int TZ>
 __global__ void __launch_bounds__(256) k_leap2d(StepArgs<T> a) {
     __shared__ T tile[TZ + 2 * H][TX + 2 * H];
     __shared__ T acc[TZ * TX];
+    __shared__ T sadd[TZ * TX];
     const int64_t blk = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
     record_receivers(a.rec, a.p, a.traces, a.nt, a.rec_step, blk * 256 + threadIdx.x);
-    leap2d_tile<T, H, TX, TZ>(a, blockIdx.x, blockIdx.y, tile, acc);
+    leap2d_tile<T, H, TX, TZ>(a, blockIdx.x, blockIdx.y, tile, acc, sadd);
 }
 
 // many shots in one launch: block -> (shot, tile) through the per-shot tile offsets
@@ -185,6 +200,7 @@ __global__ void __launch_bounds__(256) k_leap2d_batch(const StepArgs<T>* __restr
                                                       const int64_t* __restrict__ tile0, int nshot, int step) {
     __shared__ T tile[TZ + 2 * H][TX + 2 * H];
     __shared__ T acc[TZ * TX];
+    __shared__ T sadd[TZ * TX];
     const int64_t b = blockIdx.x;
     int lo = 0, hi = nshot - 1;
     while (lo < hi) {                     // last shot with tile0[s] <= b
@@ -203,7 +219,7 @@ __global__ void __launch_bounds__(256) k_leap2d_batch(const StepArgs<T>* __restr
     a.rec_step = step - 1;
     record_receivers(a.rec, a.p, a.traces, a.nt, a.rec_step, local * 256 + threadIdx.x);
     if (local >= a.ntiles) return;   // uniform per block
-    leap2d_tile<T, H, TX, TZ>(a, local % a.ntx, local / a.ntx, tile, acc);
+    leap2d_tile<T, H, TX, TZ>(a, local % a.ntx, local / a.ntx, tile, acc, sadd);
 }
 
 // receivers only (after the last step)
@@ -220,6 +236,7 @@ __global__ void __launch_bounds__(256) k_leap3d(StepArgs<T> a, int zchunk, int64
     constexpr int TX = 32, TY = 8;
     __shared__ T tile[TY + 2 * H][TX + 2 * H];
     __shared__ T acc[TY * TX];
+    __shared__ T sadd[TY * TX];
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * TX + tx;
     const int64_t blk = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
@@ -243,26 +260,27 @@ __global__ void __launch_bounds__(256) k_leap3d(StepArgs<T> a, int zchunk, int64
             if (gx < L.nx + H && gy < L.ny + H) v = a.p[L.idx(gx, gy, z)];
             tile[ly][lx] = v;
         }
+        sadd[tid] = (T)0;
         __syncthreads();
         {
-            T s = (T)3 * a.w2[0] * q[H];
+            const T c = q[H];
+            T s = 0;
 #pragma unroll
             for (int k = 1; k <= H; ++k)
-                s += a.w2[k] * ((tile[ty + H][tx + H + k] + tile[ty + H][tx + H - k]) +
-                                (tile[ty + H + k][tx + H] + tile[ty + H - k][tx + H]) + (q[H + k] + q[H - k]));
+                s += a.w2[k] * (((tile[ty + H][tx + H + k] - c) + (tile[ty + H][tx + H - k] - c)) +
+                                ((tile[ty + H + k][tx + H] - c) + (tile[ty + H - k][tx + H] - c)) +
+                                ((q[H + k] - c) + (q[H - k] - c)));
             acc[tid] = s;
         }
-        __syncthreads();
         const int64_t origin = L.idx(x0, y0, z);
+        tile_sources<T, TX, TY>(a.src, wv, origin, L.px, sadd, tid);
+        __syncthreads();
         if (a.op.ptr) add_entries(a.op, (z * nty + blockIdx.y) * a.op.ntx + blockIdx.x, a.p, origin, acc, tid, 256);
         __syncthreads();
         if (valid) {
             int64_t qi = L.idx(x, y, z);
             T c = q[H];
-            T v = c + ((c - a.pm[qi]) + a.Kh[qi] * acc[tid]);
-            for (int s = 0; s < 8 * a.src.n; ++s)
-                if (a.src.idx[s] == qi) v += a.src.w[s] * wv;
-            a.out[qi] = v;
+            a.out[qi] = c + ((c - a.pm[qi]) + a.Kh[qi] * acc[tid]) + sadd[tid];
         }
 #pragma unroll
         for (int k = 0; k < 2 * H; ++k) q[k] = q[k + 1];
@@ -348,7 +366,9 @@ __global__ void __launch_bounds__(256) k_stag_p2d(StagArgs<T> a) {
     __shared__ T tvx[TZ][TX + 2 * H];
     __shared__ T tvz[TZ + 2 * H][TX];
     __shared__ T acc[TZ * TX];
+    __shared__ T sadd[TZ * TX];
     const int tid = threadIdx.x;
+    for (int i = tid; i < TZ * TX; i += 256) sadd[i] = (T)0;
     const int64_t x0 = (int64_t)blockIdx.x * TX, z0 = (int64_t)blockIdx.y * TZ;
     const Layout& L = a.L;
     for (int i = tid; i < TZ * (TX + 2 * H); i += 256) {
@@ -379,19 +399,17 @@ __global__ void __launch_bounds__(256) k_stag_p2d(StagArgs<T> a) {
     __syncthreads();
     const int64_t tile_id = (int64_t)blockIdx.y * a.dx.ntx + blockIdx.x;
     const int64_t origin = L.base + z0 * L.px + x0;
+    const T wv = a.src.n ? a.wavelet[a.step] : (T)0;
+    tile_sources<T, TX, TZ>(a.src, wv, origin, L.px, sadd, tid);
     if (a.dx.ptr) add_entries(a.dx, tile_id, (const T*)a.vx, origin, acc, tid, 256);
     if (a.dz.ptr) add_entries(a.dz, tile_id, (const T*)a.vz, origin, acc, tid, 256);
     __syncthreads();
-    const T wv = a.src.n ? a.wavelet[a.step] : (T)0;
     for (int i = tid; i < TZ * TX; i += 256) {
         int lz = i / TX, lx = i - lz * TX;
         int64_t x = x0 + lx, z = z0 + lz;
         if (x >= L.nx || z >= L.nz) continue;
         int64_t q = origin + lz * L.px + lx;
-        T v = a.p[q] + a.kp[q] * acc[i];
-        for (int s = 0; s < 8 * a.src.n; ++s)
-            if (a.src.idx[s] == q) v += a.src.w[s] * wv;
-        a.p[q] = v;
+        a.p[q] = a.p[q] + a.kp[q] * acc[i] + sadd[i];
     }
 }
 
@@ -429,9 +447,11 @@ template <typename T, int H, int TX, int TZ>
 __global__ void __launch_bounds__(256) k_adj2d(AdjArgs<T> a) {
     __shared__ T tile[TZ + 2 * H][TX + 2 * H];
     __shared__ T acc[TZ * TX];
+    __shared__ T sw[TZ * TX];     // source weights landing in the tile
     const int tid = threadIdx.x;
     const int64_t x0 = (int64_t)blockIdx.x * TX, z0 = (int64_t)blockIdx.y * TZ;
     const Layout& L = a.L;
+    for (int i = tid; i < TZ * TX; i += 256) sw[i] = (T)0;
     for (int i = tid; i < (TZ + 2 * H) * (TX + 2 * H); i += 256) {
         int lz = i / (TX + 2 * H), lx = i - lz * (TX + 2 * H);
         int64_t x = x0 + lx - H, z = z0 + lz - H;
@@ -446,13 +466,14 @@ __global__ void __launch_bounds__(256) k_adj2d(AdjArgs<T> a) {
     for (int i = tid; i < TZ * TX; i += 256) {
         int lz = i / TX, lx = i - lz * TX;
         T c = tile[lz + H][lx + H];
-        T s = (T)2 * a.w2[0] * c;
+        T s = 0;
 #pragma unroll
         for (int k = 1; k <= H; ++k)
-            s += a.w2[k] * ((tile[lz + H][lx + H + k] + tile[lz + H][lx + H - k]) +
-                            (tile[lz + H + k][lx + H] + tile[lz + H - k][lx + H]));
+            s += a.w2[k] * (((tile[lz + H][lx + H + k] - c) + (tile[lz + H][lx + H - k] - c)) +
+                            ((tile[lz + H + k][lx + H] - c) + (tile[lz + H - k][lx + H] - c)));
         acc[i] = s;
     }
+    tile_sources<T, TX, TZ>(a.src, (T)1, L.base + z0 * L.px + x0, L.px, sw, tid);
     __syncthreads();
     const int64_t tile_id = (int64_t)blockIdx.y * a.opT.ntx + blockIdx.x;
     const int64_t origin = L.base + z0 * L.px + x0;
@@ -500,9 +521,7 @@ __global__ void __launch_bounds__(256) k_adj2d(AdjArgs<T> a) {
         T Kq = a.Kh[q];
         if (Kq > (T)0) {
             T d2 = (a.pm0[q] - a.pm1[q]) - (a.pm1[q] - a.pm2[q]);
-            T srcw = 0;
-            for (int s = 0; s < 8 * a.src.n; ++s)
-                if (a.src.idx[s] == q) srcw += a.src.w[s];
+            const T srcw = sw[i];
             d2 -= srcw * wv;
             a.grad[q] += mu_new * (a.two_dt_over_h / sqrt(Kq)) * d2;
             if (a.gw && srcw != (T)0) atomicAdd(&a.gw[a.m - 1], srcw * mu_new);
@@ -1308,3 +1327,4 @@ extern "C" ib_status ib_sync_status(void* stream) {
     if (e != cudaSuccess) return ib_cuda_fail(e, "device", __FILE__, __LINE__);
     return IB_OK;
 }
+
