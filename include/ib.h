@@ -208,6 +208,34 @@ ib_status ib_forward_batch(const ib_table* const* tables, const ib_shot* shots,
                            void* stream);
 
 /*
+ * ib_forward_noalloc -- ib_forward for callers that cannot allocate device
+ * memory (the paper has no counterpart; this is a deployment variant).  Some
+ * callers own every device allocation themselves -- a host framework with its
+ * own memory manager or a fixed device-memory budget, or a serving loop that
+ * must not allocate once it is running, since cudaMalloc/cudaFree can
+ * synchronise the device and stall other streams.  This entry point runs the
+ * 2D second-order FP32 forward of ib_forward (same shot semantics, no
+ * checkpoints) with all of its scratch (two wavefields, the coefficient
+ * field, source and receiver interpolation weights) in one file-scope device
+ * array of IB_NOALLOC_SCRATCH_BYTES = 64 MiB.  Every GPU that loads the
+ * library holds that array until the process exits.  The call makes no
+ * cudaMalloc/cudaFree or other allocating call; the table and the shot
+ * buffers are the caller's.
+ *   - Needs 3 padded fields (about 12 bytes per grid point) plus 96 bytes per
+ *     source and receiver; larger problems return IB_ERR_ARG with the sizes.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) once for that device; make that first call
+ *     before any stream capture.
+ *   - All calls share the array and it keeps the last call's contents: each
+ *     call clears what must start at zero, but calls that overlap on the GPU
+ *     (other streams, other threads) race on it and must be serialised by the
+ *     caller.
+ *   - Tables of the first-order form or 3D grids return IB_ERR_STATE.
+ */
+ib_status ib_forward_noalloc(const ib_table* table, const ib_shot* shot, double dt,
+                             int32_t nt, void* stream);
+
+/*
  * Measurement hooks (no counterpart in the paper).  ib_profile_enable(stride)
  * resets the per-kernel counters; with stride > 0 every stride-th launch of
  * each time-step kernel is bracketed by CUDA events recorded on its stream.

@@ -1328,3 +1328,142 @@ extern "C" ib_status ib_sync_status(void* stream) {
     return IB_OK;
 }
 
+// ---------------------------------------------------------------------------
+// ib_forward_noalloc: the 2D second-order FP32 forward with its scratch in a
+// file-scope device array instead of stream-ordered allocations, for callers
+// that may not allocate device memory (see include/ib.h).
+// ---------------------------------------------------------------------------
+#define IB_NOALLOC_SCRATCH_BYTES (64ll << 20)
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[IB_NOALLOC_SCRATCH_BYTES];
+
+// one warp per IB row: out[q] += Kh[q] * sum_j w_j p[q + col_j]
+__global__ void k_ib_rows_add(int64_t nrows, const int64_t* __restrict__ row_pad, const int64_t* __restrict__ row_ptr,
+                              const int64_t* __restrict__ col_pad, const float* __restrict__ w,
+                              const float* __restrict__ p, const float* __restrict__ Kh, float* out) {
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    for (int64_t r = warp; r < nrows; r += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+        const int64_t q = row_pad[r];
+        float s = 0.f;
+        for (int64_t j = row_ptr[r] + lane; j < row_ptr[r + 1]; j += 32) s += w[j] * p[q + col_pad[j]];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (lane == 0) out[q] += Kh[q] * s;
+    }
+}
+
+static std::mutex g_noalloc_mu;
+static void* g_noalloc_ptr[64] = {nullptr};
+
+// device address of the static scratch for the current device (set up once per device)
+static ib_status noalloc_scratch(unsigned char** out) {
+    int dev = 0;
+    IB_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) {
+        ib_set_error("device index out of range for the static scratch");
+        return IB_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void* ptr = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) return ib_cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)", __FILE__, __LINE__);
+        g_noalloc_ptr[dev] = ptr;
+    }
+    *out = (unsigned char*)g_noalloc_ptr[dev];
+    return IB_OK;
+}
+
+static int64_t align256(int64_t b) { return (b + 255) & ~(int64_t)255; }
+
+extern "C" ib_status ib_forward_noalloc(const ib_table* tc, const ib_shot* sh, double dt, int32_t nt, void* stream) {
+    ib_set_error("");
+    TRY(check_shot(tc, sh, 32, dt, nt));
+    ib_table* t = const_cast<ib_table*>(tc);
+    if (t->form != IB_SECOND_ORDER || t->grid.ndim != 2) {
+        ib_set_error("ib_forward_noalloc: 2D second-order tables only");
+        return IB_ERR_STATE;
+    }
+    const Layout& L = t->L;
+    const int64_t field = align256(sizeof(float) * L.total);
+    const int64_t srcb = align256(8 * (int64_t)sh->nsrc * (8 + 4));
+    const int64_t recb = align256(8 * (int64_t)sh->nrec * (8 + 4));
+    const int64_t need = 3 * field + 2 * srcb + 2 * recb + 4 * 256;
+    if (need > IB_NOALLOC_SCRATCH_BYTES) {
+        char buf[200];
+        snprintf(buf, sizeof buf, "ib_forward_noalloc: needs %lld bytes of scratch, the static limit is %lld",
+                 (long long)need, (long long)IB_NOALLOC_SCRATCH_BYTES);
+        ib_set_error(buf);
+        return IB_ERR_ARG;
+    }
+    unsigned char* base = nullptr;
+    TRY(noalloc_scratch(&base));
+    cudaStream_t s = (cudaStream_t)stream;
+    int64_t off = 0;
+    auto carve = [&](int64_t bytes) {
+        unsigned char* p = base + off;
+        off += align256(bytes);
+        return p;
+    };
+    float* p0 = (float*)carve(sizeof(float) * L.total);
+    float* p1 = (float*)carve(sizeof(float) * L.total);
+    float* Kh = (float*)carve(sizeof(float) * L.total);
+    int64_t* si = (int64_t*)carve(8 * 8 * (int64_t)std::max(sh->nsrc, 1));
+    float* sw = (float*)carve(4 * 8 * (int64_t)std::max(sh->nsrc, 1));
+    int64_t* ri = (int64_t*)carve(8 * 8 * (int64_t)std::max(sh->nrec, 1));
+    float* rw = (float*)carve(4 * 8 * (int64_t)std::max(sh->nrec, 1));
+    // every call starts from zero wavefields and a zero padding ring
+    IB_CUDA(cudaMemsetAsync(p0, 0, sizeof(float) * L.total, s));
+    IB_CUDA(cudaMemsetAsync(p1, 0, sizeof(float) * L.total, s));
+    IB_CUDA(cudaMemsetAsync(Kh, 0, sizeof(float) * L.total, s));
+    k_leap_coef<float><<<grid1(L.N, 256), 256, 0, s>>>(L, (const float*)sh->vel_dev, t->mask_pad[0], dt / t->grid.h,
+                                                       Kh);
+    if (sh->nsrc)
+        k_interp_setup<float><<<grid1(sh->nsrc, 64), 64, 0, s>>>(sh->nsrc, sh->src_dev, 2, 1.0 / t->grid.h, L,
+                                                                  t->mask_pad[0], dt * dt / (t->grid.h * t->grid.h),
+                                                                  si, sw);
+    if (sh->nrec)
+        k_interp_setup<float><<<grid1(sh->nrec, 64), 64, 0, s>>>(sh->nrec, sh->rec_dev, 2, 1.0 / t->grid.h, L,
+                                                                  t->mask_pad[0], 1.0, ri, rw);
+    IB_CHECK_LAUNCH("ib_forward_noalloc setup");
+    const int M = t->opts.space_order;
+    const int H = M / 2;
+    StepArgs<float> a;
+    memset(&a, 0, sizeof a);
+    a.L = L;
+    {
+        float c1u[4];
+        stencil_weights<float>(M, a.w2, c1u);
+    }
+    a.Kh = Kh;
+    a.src = {sh->nsrc, si, sw};
+    a.wavelet = (const float*)sh->wavelet_dev;
+    a.rec = {sh->nrec, ri, rw};
+    a.traces = (float*)sh->traces_dev;
+    a.nt = nt;
+    const IbOp& op = t->ops[0];
+    dim3 grid2((unsigned)((L.nx + TX2 - 1) / TX2), (unsigned)((L.nz + TZ2 - 1) / TZ2));
+    float* cur = p0;
+    float* prev = p1;
+    for (int n = 0; n < nt; ++n) {
+        a.p = cur;
+        a.pm = prev;
+        a.out = prev;
+        a.step = n;
+        a.rec_step = n - 1;
+        if (H == 1) k_leap2d<float, 1, TX2, TZ2><<<grid2, 256, 0, s>>>(a);
+        else if (H == 2) k_leap2d<float, 2, TX2, TZ2><<<grid2, 256, 0, s>>>(a);
+        else if (H == 3) k_leap2d<float, 3, TX2, TZ2><<<grid2, 256, 0, s>>>(a);
+        else k_leap2d<float, 4, TX2, TZ2><<<grid2, 256, 0, s>>>(a);
+        if (op.nrows)
+            k_ib_rows_add<<<grid1(op.nrows * 32, 256), 256, 0, s>>>(op.nrows, op.row_pad, op.row_ptr, op.col_pad,
+                                                                     op.w32, cur, Kh, prev);
+        IB_CHECK_LAUNCH("ib_forward_noalloc step");
+        std::swap(cur, prev);
+    }
+    if (sh->nrec)
+        k_receivers<float><<<grid1(sh->nrec, 256), 256, 0, s>>>(a.rec, cur, (float*)sh->traces_dev, nt, nt - 1);
+    IB_CHECK_LAUNCH("ib_forward_noalloc receivers");
+    return IB_OK;
+}

@@ -20,7 +20,8 @@ SECOND_ORDER, FIRST_ORDER_STAGGERED = 0, 1
 
 EXPORTS = ["ib_opts_default", "ib_build_stencils", "ib_table_free", "ib_table_stats", "ib_table_export",
            "ib_forward", "ib_checkpoint_bytes", "ib_adjoint", "ib_forward_batch", "ib_sync_status",
-           "ib_last_error", "ib_version", "ib_profile_enable", "ib_profile_count", "ib_profile_get"]
+           "ib_last_error", "ib_version", "ib_profile_enable", "ib_profile_count", "ib_profile_get",
+           "ib_forward_noalloc"]
 
 
 class IbError(RuntimeError):
@@ -101,6 +102,8 @@ def load(path=LIB_PATH):
     L.ib_profile_get.argtypes = [i32, ctypes.c_char_p, i32, ctypes.POINTER(i64), ctypes.POINTER(i64),
                                  ctypes.POINTER(dbl)]
     L.ib_profile_get.restype = i32
+    L.ib_forward_noalloc.argtypes = [vp, ctypes.POINTER(Shot), dbl, i32, vp]
+    L.ib_forward_noalloc.restype = i32
     _LIB = L
     return L
 
@@ -242,6 +245,14 @@ def ib_adjoint(table, vel, wavelet, src, rec, dt, nt, ckpt, n_ckpt, residual, wa
                              _ptr(ckpt), int(n_ckpt), _ptr(residual.contiguous()), _ptr(grad), _ptr(gw),
                              _stream(stream)))
     return grad, gw
+
+
+def ib_forward_noalloc(table, vel, wavelet, src, rec, dt, nt, traces, stream=None):
+    """ib_forward (2D second-order, FP32) with the library's static scratch: no
+    device allocation inside the call; `traces` [nrec][nt] float32 is caller-owned."""
+    sh = _shot(vel, None, src, rec, wavelet, traces)
+    _check(load().ib_forward_noalloc(table.handle, ctypes.byref(sh), float(dt), int(nt), _stream(stream)))
+    return traces
 
 
 def ib_forward_batch(tables, shots, dt, nt, stream=None):
