@@ -80,7 +80,7 @@ typedef struct {
 } ib_opts;
 
 /* Fill `opts` with the defaults for space order M (basis min(M,4), min order
- * 2, radius (basis+1)/2, growth 3, eta_p 0.5, eta_v 0, rank_tol 1e-10). */
+ * 2, radius (basis+1)/2, growth 3, eta_p 0.5, eta_v 0, rank_tol 1e-3). */
 void ib_opts_default(ib_opts* opts, int32_t space_order);
 
 typedef struct ib_table ib_table;   /* opaque, library-owned */

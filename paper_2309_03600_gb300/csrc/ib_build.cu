@@ -96,7 +96,7 @@ extern "C" void ib_opts_default(ib_opts* o, int32_t M) {
     o->growth = 3.0;
     o->eta_p = 0.5;
     o->eta_v = 0.0;
-    o->rank_tol = 1e-10;
+    o->rank_tol = 1e-3;
 }
 
 // ---------------------------------------------------------------------------
@@ -681,7 +681,7 @@ __device__ double warp_cond_ratio(const double* R, int n, double* x, double* y) 
     for (int i = lane; i < n; i += 32) x[i] = 1.0 / sqrt((double)n);
     __syncwarp();
     double smax2 = 0.0;
-    for (int it = 0; it < 8; ++it) {
+    for (int it = 0; it < 24; ++it) {
         for (int i = lane; i < n; i += 32) {
             double s = 0.0;
             for (int j = i; j < n; ++j) s += R[i * n + j] * x[j];
@@ -706,7 +706,7 @@ __device__ double warp_cond_ratio(const double* R, int n, double* x, double* y) 
     for (int i = lane; i < n; i += 32) x[i] /= nx0;
     __syncwarp();
     double smin2 = 0.0;
-    for (int it = 0; it < 10; ++it) {
+    for (int it = 0; it < 40; ++it) {
         warp_solve_RT(R, n, x);
         warp_solve_R(R, n, x);
         double nr = warp_norm(x, n);
@@ -1449,7 +1449,7 @@ static ib_status build_impl(const ib_grid* grid, const double* sdf, ib_bc bc, ib
     }
     if (o.min_order < 2 || o.min_order > o.basis_order) o.min_order = std::min(2, o.basis_order);
     if (!(o.growth >= 0.0) || o.growth > 8.0) o.growth = 3.0;
-    if (!(o.rank_tol > 0.0)) o.rank_tol = 1e-10;
+    if (!(o.rank_tol > 0.0)) o.rank_tol = 1e-3;
     if (bc != IB_FREE && bc != IB_RIGID) {
         ib_set_error("bc must be IB_FREE or IB_RIGID");
         return IB_ERR_ARG;

@@ -84,11 +84,29 @@ struct RowView {
     int64_t ntx;
 };
 
+// Each warp takes 32 consecutive entries; entries of one row are contiguous, so a
+// segmented warp sum leaves one shared-memory atomic per row segment instead of
+// one per entry (same-address atomics serialise).
 template <typename T>
 __device__ __forceinline__ void add_entries(const TileView<T>& v, int64_t tile, const T* f, int64_t origin, T* acc,
                                             int tid, int nthr) {
     const int32_t e0 = v.ptr[tile], e1 = v.ptr[tile + 1];
-    for (int32_t e = e0 + tid; e < e1; e += nthr) atomicAdd(&acc[v.loc[e]], v.w[e] * f[origin + v.src[e]]);
+    const int lane = tid & 31;
+    const int32_t step = nthr;
+    for (int32_t base = e0 + (tid & ~31); base < e1; base += step) {
+        const int32_t e = base + lane;
+        const bool valid = e < e1;
+        int32_t loc = valid ? v.loc[e] : -1 - lane;
+        T val = valid ? v.w[e] * f[origin + v.src[e]] : (T)0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            T y = __shfl_up_sync(0xffffffffu, val, o);
+            int32_t l2 = __shfl_up_sync(0xffffffffu, loc, o);
+            if (lane >= o && l2 == loc) val += y;
+        }
+        const int32_t next = __shfl_down_sync(0xffffffffu, loc, 1);
+        if (valid && (lane == 31 || next != loc)) atomicAdd(&acc[loc], val);
+    }
 }
 
 // source terms landing in a 2D tile (or one plane of a 3D tile): sadd[local] += w * wavelet

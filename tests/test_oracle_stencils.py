@@ -263,11 +263,12 @@ def test_support_grows_when_rank_deficient():
     g2 = stencils.Geometry(ws["sdf"], 5.0, 8)
     rows = stencils.divergence_rows(g2, "free", stencils.Opts(8, ib_order=8),
                                     stencils.divergence_ib_nodes(g2, 8)[:40])
-    radii = [info["radius"] for _, info in rows.values()]
-    assert max(radii) > 4.5
+    grown = [info["radius"] > (info["order"] + 1) / 2.0 or info["order"] < 8 for _, info in rows.values()]
+    assert any(grown)
     for _, info in rows.values():
         A = info["A"]
-        assert np.linalg.matrix_rank(A) == A.shape[1]
+        sv = np.linalg.svd(A, compute_uv=False)
+        assert A.shape[0] >= A.shape[1] and sv[-1] > 1e-3 * sv[0]
 
 
 def test_block_structure_coupling():
