@@ -409,7 +409,9 @@ def main():
                    "space_order": M, "bc": args.bc, "ib_rows": stats["rows"], "ib_nnz": stats["nnz"],
                    "l2": "flushed between steps (256 MB write)", "parallelism": "replicas" if world > 1 else "single"},
         "setup": {"ib_rows": setup_rows, "seconds": stats["setup_seconds"],
-                  "ib_rows_per_s": setup_rows / max(stats["setup_seconds"], 1e-9)},
+                  "ib_rows_per_s": setup_rows / max(stats["setup_seconds"], 1e-9),
+                  "rows_grown": stats["n_grown"], "rows_order_reduced": stats["n_reduced"],
+                  "rank_failures": stats["n_rank_failures"], "boundary_points": stats["n_boundary_points"]},
         "roofline": roof, "kernels": kernels, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
         "gpu_launches": int(launches), "wall_s": wall,
     }

@@ -498,22 +498,39 @@ struct FitParams {
     int64_t pool_cap;
 };
 
-__device__ __forceinline__ double mono(const double d[3], const int8_t* k, const int32_t* alpha) {
-    double v = 1.0;
+__constant__ double c_inv_int[10] = {0.0, 1.0, 0.5, 1.0 / 3.0, 0.25, 0.2, 1.0 / 6.0, 1.0 / 7.0, 0.125, 1.0 / 9.0};
+
+#define PW 9   // powers 0..8 of each coordinate (basis order <= 8)
+
+// pw[a * PW + e] = d_a^e / e!
+__device__ __forceinline__ void power_table(const double d[3], double* pw) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        int e = (int)k[a] - (alpha ? alpha[a] : 0);
-        if (e < 0) return 0.0;
-        double pw = 1.0;
-        for (int i = 1; i <= e; ++i) pw *= d[a] / (double)i;
-        v *= pw;
+        double v = 1.0;
+        pw[a * PW] = 1.0;
+#pragma unroll
+        for (int e = 1; e < PW; ++e) {
+            v *= d[a] * c_inv_int[e];
+            pw[a * PW + e] = v;
+        }
     }
-    return v;
+}
+
+// d^alpha of the monomial with exponents k, from a power table
+__device__ __forceinline__ double mono_pw(const double* pw, const int8_t* k, const int32_t* alpha) {
+    int e0 = k[0] - (alpha ? alpha[0] : 0);
+    int e1 = k[1] - (alpha ? alpha[1] : 0);
+    int e2 = k[2] - (alpha ? alpha[2] : 0);
+    if ((e0 | e1 | e2) < 0) return 0.0;
+    return pw[e0] * pw[PW + e1] * pw[2 * PW + e2];
 }
 
 struct FitSmem {
     double* R;       // [ncol][ncol]
+    double* X;       // [ncol][ncol] = R^{-1} (only when ncol <= 64, else null)
     double* B;       // [PB][ncol]
+    double* pwt;     // [PB][3 * PW] power tables of the panel rows
+    double* invd;    // [ncol] 1 / R_kk
     double* vec;     // 4 * ncol
     double* bpx;     // [FIT_MAX_BP][3] relative positions
     double* bpn;     // [FIT_MAX_BP][3]
@@ -549,46 +566,58 @@ __device__ int block_excl_scan(int v, int* tmp, int* total) {
     return before;
 }
 
-// A entry for global row gi and column col
-__device__ double a_entry(const FitParams& P, const OrderDesc& od, const FitSmem& S, int nsup,
-                          int nbcrow, int gi, int col) {
-    int f = col / od.T;
-    int k = col - f * od.T;
-    const int8_t* K = od.K + 3 * k;
+// position of global row gi of A relative to x0 (grid units)
+__device__ __forceinline__ void row_delta(const FitParams& P, const FitSmem& S, int nsup, int nbcrow, int gi,
+                                          double d[3]) {
     if (gi < nsup) {
-        int32_t s = S.sup[gi];
-        int sf = s >> 24;
-        if (sf != f) return 0.0;
+        int32_t c = S.sup[gi];
+        int f = c >> 24;
         int dx, dy, dz;
-        unpack_off(s & 0xffffff, dx, dy, dz);
+        unpack_off(c & 0xffffff, dx, dy, dz);
         int o[3] = {dx, dy, dz};
-        double d[3];
         for (int a = 0; a < 3; ++a)
             d[a] = a < P.g.ndim ? 0.5 * (double)(2 * o[a] + P.fshift2[f][a] - P.x0shift2[a]) : 0.0;
-        return mono(d, K, nullptr);
+    } else {
+        int b = (gi - nsup) / nbcrow;
+        for (int a = 0; a < 3; ++a) d[a] = S.bpx[3 * b + a];
     }
-    int j = gi - nsup;
-    int b = j / nbcrow;
-    int r = j - b * nbcrow;
-    const double* d = S.bpx + 3 * b;
+}
+
+// A entry of global row gi, column col, from the row's power table
+__device__ __forceinline__ double a_entry_pw(const FitParams& P, const OrderDesc& od, const FitSmem& S, int nsup,
+                                             int nbcrow, int gi, int col, const double* pw) {
+    const int f = col / od.T;
+    const int k = col - f * od.T;
+    const int8_t* K = od.K + 3 * k;
+    if (gi < nsup) return ((S.sup[gi] >> 24) == f) ? mono_pw(pw, K, nullptr) : 0.0;
+    const int j = gi - nsup;
+    const int b = j / nbcrow;
+    const int r = j - b * nbcrow;
     const double* nn = S.bpn + 3 * b;
     double v = 0.0;
     for (int t = od.row_start[r]; t < od.row_start[r + 1]; ++t) {
         const DevTerm& tm = od.terms[t];
         if (tm.field != f) continue;
-        double c = tm.coef * (tm.axis >= 0 ? nn[tm.axis] : 1.0);
-        if (c == 0.0) continue;
-        v += c * mono(d, K, tm.alpha);
+        const double c = tm.coef * (tm.axis >= 0 ? nn[tm.axis] : 1.0);
+        if (c != 0.0) v += c * mono_pw(pw, K, tm.alpha);
     }
     return v;
 }
 
+// rows row0 .. row0 + PB - 1 of A into the panel B (zero rows past m)
 __device__ void build_panel(const FitParams& P, const OrderDesc& od, const FitSmem& S, int nsup,
                             int nbcrow, int m, int row0, int ncol) {
+    for (int i = threadIdx.x; i < FIT_PB; i += blockDim.x) {
+        int gi = row0 + i;
+        double d[3] = {0.0, 0.0, 0.0};
+        if (gi < m) row_delta(P, S, nsup, nbcrow, gi, d);
+        power_table(d, S.pwt + i * 3 * PW);
+    }
+    __syncthreads();
     for (int idx = threadIdx.x; idx < FIT_PB * ncol; idx += blockDim.x) {
         int i = idx / ncol, col = idx - i * ncol;
         int gi = row0 + i;
-        S.B[idx] = gi < m ? a_entry(P, od, S, nsup, nbcrow, gi, col) : 0.0;
+        S.B[idx] = gi < m ? a_entry_pw(P, od, S, nsup, nbcrow, gi, col, S.pwt + i * 3 * PW) : 0.0;
     }
 }
 
@@ -635,20 +664,20 @@ __device__ void qr_panel(const FitSmem& S, int ncol) {
 }
 
 // warp-level triangular solves on R (row-major, upper), vector in shared memory
-__device__ void warp_solve_RT(const double* R, int n, double* x) {   // R^T w = x
+__device__ void warp_solve_RT(const double* R, const double* invd, int n, double* x) {   // R^T w = x
     int lane = threadIdx.x & 31;
     for (int k = 0; k < n; ++k) {
-        double wk = x[k] / R[k * n + k];
+        double wk = x[k] * invd[k];
         __syncwarp();
         if (lane == 0) x[k] = wk;
         for (int i = k + 1 + lane; i < n; i += 32) x[i] -= R[k * n + i] * wk;
         __syncwarp();
     }
 }
-__device__ void warp_solve_R(const double* R, int n, double* x) {    // R y = x
+__device__ void warp_solve_R(const double* R, const double* invd, int n, double* x) {    // R y = x
     int lane = threadIdx.x & 31;
     for (int k = n - 1; k >= 0; --k) {
-        double yk = x[k] / R[k * n + k];
+        double yk = x[k] * invd[k];
         __syncwarp();
         if (lane == 0) x[k] = yk;
         for (int i = lane; i < k; i += 32) x[i] -= R[i * n + k] * yk;
@@ -662,22 +691,9 @@ __device__ double warp_norm(const double* x, int n) {
     return sqrt(s);
 }
 
-// rank test on R: returns sigma_min / sigma_max estimate (0 if singular); warp 0
-__device__ double warp_cond_ratio(const double* R, int n, double* x, double* y) {
+// sigma_min / sigma_max of R by power / inverse iteration in one warp (large n)
+__device__ double warp_cond_ratio(const double* R, const double* invd, int n, double* x, double* y) {
     int lane = threadIdx.x & 31;
-    double dmax = 0.0;
-    bool zero = false;
-    for (int i = lane; i < n; i += 32) {
-        double d = fabs(R[i * n + i]);
-        dmax = fmax(dmax, d);
-        zero |= (d == 0.0);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-        dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-        zero |= __shfl_xor_sync(0xffffffffu, (int)zero, o);
-    }
-    if (zero || dmax == 0.0) return 0.0;
-    // sigma_max: power iteration on R^T R
     for (int i = lane; i < n; i += 32) x[i] = 1.0 / sqrt((double)n);
     __syncwarp();
     double smax2 = 0.0;
@@ -699,7 +715,6 @@ __device__ double warp_cond_ratio(const double* R, int n, double* x, double* y) 
         for (int i = lane; i < n; i += 32) x[i] /= nr;
         __syncwarp();
     }
-    // sigma_min: inverse iteration with (R^T R)^{-1}
     for (int i = lane; i < n; i += 32) x[i] = 1.0 / sqrt((double)n) * (1.0 + 0.01 * (i % 7));
     __syncwarp();
     double nx0 = warp_norm(x, n);
@@ -707,8 +722,8 @@ __device__ double warp_cond_ratio(const double* R, int n, double* x, double* y) 
     __syncwarp();
     double smin2 = 0.0;
     for (int it = 0; it < 40; ++it) {
-        warp_solve_RT(R, n, x);
-        warp_solve_R(R, n, x);
+        warp_solve_RT(R, invd, n, x);
+        warp_solve_R(R, invd, n, x);
         double nr = warp_norm(x, n);
         if (!(nr < 1e300) || nr == 0.0) return 0.0;
         smin2 = 1.0 / nr;
@@ -718,17 +733,94 @@ __device__ double warp_cond_ratio(const double* R, int n, double* x, double* y) 
     return sqrt(smin2 / smax2);
 }
 
+// X = R^{-1} (upper triangular): thread j back-substitutes column j
+__device__ void tri_inverse(const double* R, const double* invd, double* X, int n) {
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        for (int i = n - 1; i > j; --i) X[i * n + j] = 0.0;
+        X[j * n + j] = invd[j];
+        for (int i = j - 1; i >= 0; --i) {
+            double s = 0.0;
+            for (int k = i + 1; k <= j; ++k) s += R[i * n + k] * X[k * n + j];
+            X[i * n + j] = -s * invd[i];
+        }
+    }
+}
+
+__device__ double block_sum(double v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    __syncthreads();
+    if ((threadIdx.x & 31) == 0) red[w] = v;
+    __syncthreads();
+    double t = 0.0;
+    for (int i = 0; i < nw; ++i) t += red[i];
+    return t;
+}
+
+// largest singular value of an upper-triangular M by power iteration on M^T M (block-parallel)
+__device__ double block_sigma_max(const double* M, int n, double* v, double* w, double* red, int iters) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = 1.0 + 0.01 * (i % 5);
+    __syncthreads();
+    double nrm = sqrt(block_sum([&] {
+        double t = 0.0;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) t += v[i] * v[i];
+        return t;
+    }(), red));
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] /= nrm;
+    __syncthreads();
+    double lam = 0.0;
+    for (int it = 0; it < iters; ++it) {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            double t = 0.0;
+            for (int j = i; j < n; ++j) t += M[i * n + j] * v[j];
+            w[i] = t;
+        }
+        __syncthreads();
+        double t2 = 0.0;
+        for (int j = threadIdx.x; j < n; j += blockDim.x) {
+            double t = 0.0;
+            for (int i = 0; i <= j; ++i) t += M[i * n + j] * w[i];
+            v[j] = t;
+            t2 += t * t;
+        }
+        lam = sqrt(block_sum(t2, red));    // |M^T M v| -> sigma_max^2
+        if (!(lam > 0.0) || !(lam < 1e300)) return lam;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] /= lam;
+        __syncthreads();
+    }
+    return sqrt(lam);
+}
+
+// z = X (X^T y) with X = R^{-1}: the solve (R^T R) z = y by two triangular matvecs
+__device__ void x_solve(const double* X, int n, const double* y, double* t, double* z) {
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        double s = 0.0;
+        for (int i = 0; i <= j; ++i) s += X[i * n + j] * y[i];
+        t[j] = s;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        double s = 0.0;
+        for (int j = i; j < n; ++j) s += X[i * n + j] * t[j];
+        z[i] = s;
+    }
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(FIT_THREADS) k_fit(FitParams P) {
     extern __shared__ double smem_d[];
     const int ncm = P.ncol_max;
     FitSmem S;
     S.R = smem_d;
-    S.B = S.R + ncm * ncm;
-    S.vec = S.B + FIT_PB * ncm;
+    S.X = ncm <= 64 ? S.R + ncm * ncm : nullptr;
+    S.B = S.R + ncm * ncm * (ncm <= 64 ? 2 : 1);
+    S.pwt = S.B + FIT_PB * ncm;
+    S.invd = S.pwt + FIT_PB * 3 * PW;
+    S.vec = S.invd + ncm;
     S.bpx = S.vec + 4 * ncm;
     S.bpn = S.bpx + 3 * FIT_MAX_BP;
-    S.scald = S.bpn + 3 * FIT_MAX_BP;
-    S.sup = (int32_t*)(S.scald + 8);
+    S.scald = S.bpn + 3 * FIT_MAX_BP;     // [48]: 0..7 scalars, 4..7 block_sum scratch, 16..47 panel dots
+    S.sup = (int32_t*)(S.scald + 48);
     S.bps = S.sup + FIT_MAX_SUP;
     S.scal = S.bps + FIT_MAX_BP;          // [0..63]
     int* scan_tmp = S.scal + 16;
@@ -889,18 +981,41 @@ __global__ void __launch_bounds__(FIT_THREADS) k_fit(FitParams P) {
                     __syncthreads();
                     qr_panel(S, ncol);
                 }
-                // ---- rank test
-                if (threadIdx.x < 32) {
-                    double ratio = warp_cond_ratio(S.R, ncol, S.vec, S.vec + ncm);
-                    if (threadIdx.x == 0) S.scald[4] = ratio;
+                // ---- rank test: sigma_min / sigma_max of R
+                for (int k = threadIdx.x; k < ncol; k += blockDim.x) {
+                    double rkk = S.R[k * ncol + k];
+                    S.invd[k] = rkk != 0.0 ? 1.0 / rkk : 0.0;
+                }
+                if (threadIdx.x == 0) S.scal[3] = 0;
+                __syncthreads();
+                for (int k = threadIdx.x; k < ncol; k += blockDim.x)
+                    if (S.invd[k] == 0.0) S.scal[3] = 1;
+                __syncthreads();
+                double ratio = 0.0;
+                const bool singular = S.scal[3] != 0;
+                if (!singular) {
+                    if (S.X) {
+                        tri_inverse(S.R, S.invd, S.X, ncol);
+                        __syncthreads();
+                        double smax = block_sigma_max(S.R, ncol, S.vec, S.vec + ncm, S.scald + 8 - 4, 30);
+                        double sinv = block_sigma_max(S.X, ncol, S.vec, S.vec + ncm, S.scald + 8 - 4, 30);
+                        ratio = (smax > 0.0 && sinv > 0.0 && sinv < 1e300) ? 1.0 / (smax * sinv) : 0.0;
+                    } else {
+                        if (threadIdx.x < 32) {
+                            double rr = warp_cond_ratio(S.R, S.invd, ncol, S.vec, S.vec + ncm);
+                            if (threadIdx.x == 0) S.scald[4] = rr;
+                        }
+                        __syncthreads();
+                        ratio = S.scald[4];
+                    }
                 }
                 __syncthreads();
-                const double ratio = S.scald[4];
                 if (!(ratio > P.rank_tol)) continue;
                 // ---- right-hand side u = sum_e w_e a(x_e - x0)
                 double* u = S.vec;              // [ncol]
                 double* z = S.vec + ncm;        // [ncol]
                 double* rho = S.vec + 2 * ncm;  // [ncol]
+                double* tv = S.vec + 3 * ncm;   // [ncol] scratch
                 for (int col = threadIdx.x; col < ncol; col += blockDim.x) {
                     int f = col / od.T;
                     int k = col - f * od.T;
@@ -908,37 +1023,41 @@ __global__ void __launch_bounds__(FIT_THREADS) k_fit(FitParams P) {
                     for (int e = 0; e < P.rule.nE; ++e) {
                         if (!((emask >> e) & 1u)) continue;
                         int ef = P.rule.Efield[e];
-                        // unknown field index of this stencil point's field kind
-                        int fi = 0;
+                        int fi = 0;   // unknown field index of this stencil point's field kind
                         for (int ff = 0; ff < P.nf; ++ff)
                             if (P.fkind[ff] == ef) fi = ff;
                         if (fi != f) continue;
-                        double d[3];
+                        double d[3], pw[3 * PW];
                         for (int a = 0; a < 3; ++a)
                             d[a] = a < P.g.ndim ? 0.5 * (double)(2 * P.rule.Eoff[e][a] + P.fshift2[f][a] - P.x0shift2[a]) : 0.0;
-                        acc += P.rule.Ew[e] * mono(d, od.K + 3 * k, nullptr);
+                        power_table(d, pw);
+                        acc += P.rule.Ew[e] * mono_pw(pw, od.K + 3 * k, nullptr);
                     }
                     u[col] = acc;
                     z[col] = acc;
                 }
                 __syncthreads();
-                if (threadIdx.x < 32) {
-                    warp_solve_RT(S.R, ncol, z);
-                    warp_solve_R(S.R, ncol, z);
+                if (S.X) {
+                    x_solve(S.X, ncol, u, tv, z);
+                } else {
+                    if (threadIdx.x < 32) {
+                        warp_solve_RT(S.R, S.invd, ncol, z);
+                        warp_solve_R(S.R, S.invd, ncol, z);
+                    }
+                    __syncthreads();
                 }
-                __syncthreads();
                 // ---- one refinement step: rho = u - A^T (A z); z += (R^T R)^{-1} rho
                 for (int col = threadIdx.x; col < ncol; col += blockDim.x) rho[col] = u[col];
                 __syncthreads();
-                double* s_i = S.vec + 3 * ncm;   // [FIT_PB] (ncm >= FIT_PB)
+                double* s_i = S.scald + 16;      // [FIT_PB]
                 for (int row0 = 0; row0 < m; row0 += FIT_PB) {
                     build_panel(P, od, S, nsup, nbcrow, m, row0, ncol);
                     __syncthreads();
                     for (int i = threadIdx.x >> 5; i < FIT_PB; i += blockDim.x >> 5) {
-                        double s = 0.0;
-                        for (int col = threadIdx.x & 31; col < ncol; col += 32) s += S.B[i * ncol + col] * z[col];
-                        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-                        if ((threadIdx.x & 31) == 0) s_i[i] = s;
+                        double sacc = 0.0;
+                        for (int col = threadIdx.x & 31; col < ncol; col += 32) sacc += S.B[i * ncol + col] * z[col];
+                        for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+                        if ((threadIdx.x & 31) == 0) s_i[i] = sacc;
                     }
                     __syncthreads();
                     for (int col = threadIdx.x; col < ncol; col += blockDim.x) {
@@ -948,12 +1067,17 @@ __global__ void __launch_bounds__(FIT_THREADS) k_fit(FitParams P) {
                     }
                     __syncthreads();
                 }
-                if (threadIdx.x < 32) {
-                    warp_solve_RT(S.R, ncol, rho);
-                    warp_solve_R(S.R, ncol, rho);
+                if (S.X) {
+                    x_solve(S.X, ncol, rho, tv, u);          // u <- correction (u no longer needed)
+                    for (int col = threadIdx.x; col < ncol; col += blockDim.x) z[col] += u[col];
+                } else {
+                    if (threadIdx.x < 32) {
+                        warp_solve_RT(S.R, S.invd, ncol, rho);
+                        warp_solve_R(S.R, S.invd, ncol, rho);
+                    }
+                    __syncthreads();
+                    for (int col = threadIdx.x; col < ncol; col += blockDim.x) z[col] += rho[col];
                 }
-                __syncthreads();
-                for (int col = threadIdx.x; col < ncol; col += blockDim.x) z[col] += rho[col];
                 __syncthreads();
                 // ---- output: y_i = A_i z for interior rows
                 if (threadIdx.x == 0) {
@@ -968,13 +1092,21 @@ __global__ void __launch_bounds__(FIT_THREADS) k_fit(FitParams P) {
                     done = true;
                     break;
                 }
-                for (int i = threadIdx.x; i < nsup; i += blockDim.x) {
-                    int f = S.sup[i] >> 24;
-                    double s = 0.0;
-                    for (int k = 0; k < od.T; ++k) s += a_entry(P, od, S, nsup, nbcrow, i, f * od.T + k) * z[f * od.T + k];
-                    P.pool_code[start + i] = S.sup[i] & 0xffffff;
-                    P.pool_field[start + i] = (int8_t)f;
-                    P.pool_w[start + i] = s;
+                for (int row0 = 0; row0 < nsup; row0 += FIT_PB) {
+                    build_panel(P, od, S, nsup, nbcrow, nsup, row0, ncol);
+                    __syncthreads();
+                    for (int i = threadIdx.x >> 5; i < FIT_PB && row0 + i < nsup; i += blockDim.x >> 5) {
+                        double sacc = 0.0;
+                        for (int col = threadIdx.x & 31; col < ncol; col += 32) sacc += S.B[i * ncol + col] * z[col];
+                        for (int o = 16; o > 0; o >>= 1) sacc += __shfl_xor_sync(0xffffffffu, sacc, o);
+                        if ((threadIdx.x & 31) == 0) {
+                            const int gi = row0 + i;
+                            P.pool_code[start + gi] = S.sup[gi] & 0xffffff;
+                            P.pool_field[start + gi] = (int8_t)(S.sup[gi] >> 24);
+                            P.pool_w[start + gi] = sacc;
+                        }
+                    }
+                    __syncthreads();
                 }
                 if (threadIdx.x == 0) P.start[row] = start;
                 status = 0;
@@ -1318,8 +1450,9 @@ static ib_status run_fit(ib_table* t, const Geo& g, const FitKind& fk, const int
         P.pool_w = pool_w;
         P.pool_top = top;
         P.pool_cap = cap;
-        size_t shm = sizeof(double) * ((size_t)P.ncol_max * P.ncol_max + (size_t)FIT_PB * P.ncol_max +
-                                       4 * (size_t)P.ncol_max + 6 * FIT_MAX_BP + 8) +
+        size_t ncm = (size_t)P.ncol_max;
+        size_t shm = sizeof(double) * (ncm * ncm * (ncm <= 64 ? 2 : 1) + (size_t)FIT_PB * ncm + FIT_PB * 3 * PW +
+                                       ncm + 4 * ncm + 6 * FIT_MAX_BP + 48) +
                      sizeof(int32_t) * (FIT_MAX_SUP + FIT_MAX_BP + 64);
         IB_CUDA(cudaFuncSetAttribute(k_fit, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)shm));
         if (nrows > 0) {

@@ -84,28 +84,44 @@ struct RowView {
     int64_t ntx;
 };
 
-// Each warp takes 32 consecutive entries; entries of one row are contiguous, so a
-// segmented warp sum leaves one shared-memory atomic per row segment instead of
-// one per entry (same-address atomics serialise).
+// Each warp takes chunks of 32 consecutive entries, four chunks at a time so that
+// four independent gathers are in flight per thread (surface tiles carry
+// thousands of entries and would otherwise serialise on memory latency).
+// Entries of one row are contiguous, so a segmented warp sum leaves one
+// shared-memory atomic per row segment instead of one per entry.
+template <typename T>
+__device__ __forceinline__ void seg_add(T* acc, int32_t loc, T val, bool valid, int lane) {
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        T y = __shfl_up_sync(0xffffffffu, val, o);
+        int32_t l2 = __shfl_up_sync(0xffffffffu, loc, o);
+        if (lane >= o && l2 == loc) val += y;
+    }
+    const int32_t next = __shfl_down_sync(0xffffffffu, loc, 1);
+    if (valid && (lane == 31 || next != loc)) atomicAdd(&acc[loc], val);
+}
+
 template <typename T>
 __device__ __forceinline__ void add_entries(const TileView<T>& v, int64_t tile, const T* f, int64_t origin, T* acc,
                                             int tid, int nthr) {
+    constexpr int U = 4;
     const int32_t e0 = v.ptr[tile], e1 = v.ptr[tile + 1];
     const int lane = tid & 31;
-    const int32_t step = nthr;
-    for (int32_t base = e0 + (tid & ~31); base < e1; base += step) {
-        const int32_t e = base + lane;
-        const bool valid = e < e1;
-        int32_t loc = valid ? v.loc[e] : -1 - lane;
-        T val = valid ? v.w[e] * f[origin + v.src[e]] : (T)0;
+    const int32_t warp_base = (tid & ~31) * U;
+    const int32_t step = nthr * U;
+    for (int32_t base = e0 + warp_base; base < e1; base += step) {
+        int32_t loc[U];
+        T val[U];
+        bool ok[U];
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            T y = __shfl_up_sync(0xffffffffu, val, o);
-            int32_t l2 = __shfl_up_sync(0xffffffffu, loc, o);
-            if (lane >= o && l2 == loc) val += y;
+        for (int u = 0; u < U; ++u) {
+            const int32_t e = base + u * 32 + lane;
+            ok[u] = e < e1;
+            loc[u] = ok[u] ? v.loc[e] : -1 - lane;
+            val[u] = ok[u] ? v.w[e] * f[origin + v.src[e]] : (T)0;
         }
-        const int32_t next = __shfl_down_sync(0xffffffffu, loc, 1);
-        if (valid && (lane == 31 || next != loc)) atomicAdd(&acc[loc], val);
+#pragma unroll
+        for (int u = 0; u < U; ++u) seg_add(acc, loc[u], val[u], ok[u], lane);
     }
 }
 
