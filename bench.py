@@ -36,9 +36,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="stag2d", choices=["stag2d", "hills3d", "flat2d"])
+    ap.add_argument("--workload", default="stag2d",
+                    choices=["stag2d", "hills3d", "flat2d", "batch2d", "adjoint2d"])
+    ap.add_argument("--nshot", type=int, default=48, help="shots of batch2d / adjoint2d")
     ap.add_argument("--bc", default="free", choices=["free", "rigid"])
     ap.add_argument("--nt", type=int, default=0, help="override time steps (testing only)")
+    ap.add_argument("--grid", type=int, nargs="*", default=None,
+                    help="override the grid (nx ny nz) of hills3d (profiling of smaller cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -47,7 +51,7 @@ def parse():
 # ---------------------------------------------------------------------------
 # workloads
 # ---------------------------------------------------------------------------
-def make_workload(name, bc, rank=0, nt=0):
+def make_workload(name, bc, rank=0, nt=0, grid=None):
     from paper_2309_03600_gb300 import inputs
     if name == "stag2d":
         w = inputs.workload_sinusoid_staggered(bc=bc, seed=2 + 1000 * rank)
@@ -55,7 +59,8 @@ def make_workload(name, bc, rank=0, nt=0):
         w["desc"] = ("2D first-order staggered p-v, 1001x1001, h=5 m, order 8, FP32, 3000 steps, "
                      "sinusoid %s surface, 4 layers, 12 Hz Ricker, 500 receivers" % bc)
     elif name == "hills3d":
-        w = inputs.workload_hills3d(bc=bc, seed=3 + 1000 * rank, device="cuda")
+        kw = dict(nx=grid[0], ny=grid[1], nz=grid[2]) if grid else {}
+        w = inputs.workload_hills3d(bc=bc, seed=3 + 1000 * rank, device="cuda", **kw)
         w["form"] = "second"
         w["rho"] = None
         w["desc"] = ("3D second-order, 512x512x384, h=10 m, order 8, FP32, 2000 steps at CFL 0.45, "
@@ -286,8 +291,10 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
+    if args.workload in ("batch2d", "adjoint2d"):
+        return run_shots(args, world, rank, local, dev, dist)
 
-    w = make_workload(args.workload, args.bc, rank, args.nt)
+    w = make_workload(args.workload, args.bc, rank, args.nt, args.grid)
     dtype = torch.float64 if w["dtype"] == "f64" else torch.float32
     eb = 8 if dtype == torch.float64 else 4
     nt = w["nt"]
@@ -414,6 +421,139 @@ def main():
                   "rank_failures": stats["n_rank_failures"], "boundary_points": stats["n_boundary_points"]},
         "roofline": roof, "kernels": kernels, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
         "gpu_launches": int(launches), "wall_s": wall,
+    }
+    print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_shots(args, world, rank, local, dev, dist):
+    """batch2d: many 2D second-order shots (sides in [400, 1200], order 8, FP32,
+    2000 steps) in one batched, graph-captured launch per step; one step = the
+    forward of all shots (tables built once, reported as setup).  The same shots
+    one launch per shot and step are timed once for comparison.
+    adjoint2d: the same shots one after the other, forward with 40 checkpoints +
+    adjoint (velocity gradient of the L2 misfit); one step = all shots."""
+    import torch
+    from paper_2309_03600_gb300 import ib, inputs
+    nt = args.nt or 2000
+    shots, tables = [], []
+    t_setup = 0.0
+    for k in range(args.nshot):
+        w = inputs.workload_shot2d(k + 1000 * rank, nt=nt, device="cuda")
+        t0 = time.perf_counter()
+        t = ib.ib_build_stencils(torch.as_tensor(w["sdf"], dtype=torch.float64, device=dev), w["h"], "free",
+                                 "second", w["M"])
+        torch.cuda.synchronize()
+        t_setup += time.perf_counter() - t0
+        tables.append(t)
+        shots.append(dict(vel=torch.as_tensor(w["vel"], dtype=torch.float32, device=dev),
+                          wavelet=torch.as_tensor(w["wavelet"], dtype=torch.float32, device=dev),
+                          src=torch.as_tensor(w["src"], dtype=torch.float64, device=dev),
+                          rec=torch.as_tensor(w["rec"], dtype=torch.float64, device=dev),
+                          N=w["shape"][0] * w["shape"][1], dt=w["dt"]))
+    dt = shots[0]["dt"]
+    N = sum(sh["N"] for sh in shots)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    n_ckpt = 40
+    ckpts = []
+    if args.workload == "adjoint2d":
+        for t in tables:
+            ckpts.append(torch.empty(ib.ib_checkpoint_bytes(t, 32, nt, n_ckpt), dtype=torch.uint8, device=dev))
+
+    def step():
+        if args.workload == "batch2d":
+            ib.ib_forward_batch(tables, shots, dt, nt)
+        else:
+            for t, sh, ck in zip(tables, shots, ckpts):
+                tr = ib.ib_forward(t, sh["vel"], sh["wavelet"], sh["src"], sh["rec"], dt, nt, ckpt=ck,
+                                   n_ckpt=n_ckpt)
+                ib.ib_adjoint(t, sh["vel"], sh["wavelet"], sh["src"], sh["rec"], dt, nt, ck, n_ckpt, tr)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    ib.ib_profile_enable(8)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        step()
+        e1.record(stream)
+        ev.append((e0, e1))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    prof = ib.ib_profile()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
+    if dist:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    value = world * N * nt / (ms * 1e-3)
+    kernels = {k: {"launches": d["launches"], "avg_us": 1e3 * d["sampled_ms"] / d["sampled"]}
+               for k, d in prof.items() if d["sampled"]}
+    peak, peak_kind = peaks()
+    roof = None
+    compare = None
+    if args.workload == "batch2d":
+        g = prof.get("leap2d_batch_graph_f32")
+        if g and g["sampled"]:
+            per_launch = g["sampled_ms"] / g["sampled"] / nt * 1e-3
+            byts = 16.0 * N + sum(t.stats()["nnz"][0] * 12 + t.stats()["rows"][0] * 20 for t in tables)
+            ach = byts / per_launch / 1e9
+            roof = {"bound": "hbm", "kernel": "leap2d_batch_f32", "achieved": ach, "peak": peak,
+                    "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / peak, "traffic": None,
+                    "algorithmic_bytes_per_launch": byts, "avg_launch_us": per_launch * 1e6,
+                    "frac_of_nominal_8TBs": ach / 8000.0}
+        # the same shots, one launch per shot and time step
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for t, sh in zip(tables, shots):
+            ib.ib_forward(t, sh["vel"], sh["wavelet"], sh["src"], sh["rec"], dt, nt)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms1 = e0.elapsed_time(e1)
+        compare = {"one_shot_per_launch_value": N * nt / (ms1 * 1e-3), "one_shot_per_launch_ms": ms1,
+                   "batched_speedup": ms1 / ms}
+    else:
+        a = prof.get("adj2d_f32")
+        if a and a["sampled"]:
+            avg = a["sampled_ms"] / a["sampled"] * 1e-3
+            # adjoint kernel: mu, mu_prev, Kh, mask, three stored p, grad RMW, mu_next per point
+            avg_N = N / len(shots)
+            byts = (4 * 7 + 1 + 4) * avg_N
+            ach = byts / avg / 1e9
+            roof = {"bound": "hbm", "kernel": "adj2d_f32", "achieved": ach, "peak": peak, "peak_kind": peak_kind,
+                    "unit": "GB/s", "frac": ach / peak, "traffic": None, "algorithmic_bytes_per_launch": byts,
+                    "avg_launch_us": avg * 1e6, "frac_of_nominal_8TBs": ach / 8000.0}
+    if rank != 0:
+        return 0
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "shots": len(shots), "points": N, "nt": nt, "space_order": 8,
+                   "step": ("batched forward of all shots (tables prebuilt)" if args.workload == "batch2d"
+                            else "forward with 40 checkpoints + adjoint gradient, all shots"),
+                   "l2": "flushed between steps (256 MB write)"},
+        "setup": {"seconds": t_setup, "ib_rows": sum(t.stats()["rows"][0] for t in tables)},
+        "roofline": roof, "kernels": kernels, "compare": compare, "e2e": None, "cpu_baseline": None,
+        "clocks": clk, "gpu_launches": int(sum(d["launches"] for d in prof.values())),
     }
     print(json.dumps(out))
     if dist:
