@@ -288,6 +288,7 @@ static HostTemplate bc_template(bool vector, ib_bc bc, int d, int M) {
 #define FIT_MAX_BP 256
 #define FIT_PB 32
 #define FIT_THREADS 128
+static_assert(FIT_THREADS == 4 * 32 && FIT_PB % 4 == 0, "qr_panel maps 32 columns x 4 row quarters onto the block");
 #define FIT_MAX_COL 128
 
 struct OrderDesc {
@@ -648,13 +649,31 @@ __device__ void qr_panel(const FitSmem& S, int ncol) {
         __syncthreads();
         double tau = S.scald[0];
         if (tau != 0.0) {
-            double v0 = S.scald[1];
-            for (int j = k + 1 + threadIdx.x; j < ncol; j += blockDim.x) {
-                double w = v0 * R[k * ncol + j];
-                for (int i = 0; i < FIT_PB; ++i) w += B[i * ncol + k] * B[i * ncol + j];
-                w *= tau;
-                R[k * ncol + j] -= v0 * w;
-                for (int i = 0; i < FIT_PB; ++i) B[i * ncol + j] -= B[i * ncol + k] * w;
+            // thread = (column c of 32, row quarter g of the panel): four lanes share a
+            // column, so every lane of a warp carries a column while columns remain
+            const double v0 = S.scald[1];
+            const int g = threadIdx.x & 3, c = threadIdx.x >> 2;
+            const int wfirst = (threadIdx.x >> 5) * 8;       // first column offset of this warp
+            double bk[FIT_PB / 4];
+#pragma unroll
+            for (int r = 0; r < FIT_PB / 4; ++r) bk[r] = B[(g * (FIT_PB / 4) + r) * ncol + k];
+            for (int jb = k + 1; jb + wfirst < ncol; jb += 32) {
+                const int j = jb + c;
+                const bool act = j < ncol;
+                double w = 0.0;
+                if (act) {
+#pragma unroll
+                    for (int r = 0; r < FIT_PB / 4; ++r) w += bk[r] * B[(g * (FIT_PB / 4) + r) * ncol + j];
+                    if (g == 0) w += v0 * R[k * ncol + j];
+                }
+                w += __shfl_xor_sync(0xffffffffu, w, 1);
+                w += __shfl_xor_sync(0xffffffffu, w, 2);
+                if (act) {
+                    w *= tau;
+                    if (g == 0) R[k * ncol + j] -= v0 * w;
+#pragma unroll
+                    for (int r = 0; r < FIT_PB / 4; ++r) B[(g * (FIT_PB / 4) + r) * ncol + j] -= bk[r] * w;
+                }
             }
         }
         __syncthreads();
@@ -757,38 +776,49 @@ __device__ double block_sum(double v, double* red) {
     return t;
 }
 
-// largest singular value of an upper-triangular M by power iteration on M^T M (block-parallel)
-__device__ double block_sigma_max(const double* M, int n, double* v, double* w, double* red, int iters) {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = 1.0 + 0.01 * (i % 5);
+__device__ float block_sum_f(float v, double* red) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    const int w = threadIdx.x >> 5, nw = blockDim.x >> 5;
     __syncthreads();
-    double nrm = sqrt(block_sum([&] {
-        double t = 0.0;
-        for (int i = threadIdx.x; i < n; i += blockDim.x) t += v[i] * v[i];
-        return t;
-    }(), red));
+    if ((threadIdx.x & 31) == 0) red[w] = (double)v;
+    __syncthreads();
+    float t = 0.f;
+    for (int i = 0; i < nw; ++i) t += (float)red[i];
+    return t;
+}
+
+// largest singular value of an upper-triangular M (row-major, FP64 in shared
+// memory) by power iteration on M^T M in FP32: the rank decision needs a few
+// digits, and GB300's FP64 pipe is the constructor's bottleneck
+__device__ float block_sigma_max(const double* M, int n, float* v, float* w, double* red, int iters) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = 1.f + 0.01f * (float)(i % 5);
+    __syncthreads();
+    float t0 = 0.f;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) t0 += v[i] * v[i];
+    float nrm = sqrtf(block_sum_f(t0, red));
     for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] /= nrm;
     __syncthreads();
-    double lam = 0.0;
+    float lam = 0.f;
     for (int it = 0; it < iters; ++it) {
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
-            double t = 0.0;
-            for (int j = i; j < n; ++j) t += M[i * n + j] * v[j];
+            float t = 0.f;
+            for (int j = i; j < n; ++j) t += (float)M[i * n + j] * v[j];
             w[i] = t;
         }
         __syncthreads();
-        double t2 = 0.0;
+        float t2 = 0.f;
         for (int j = threadIdx.x; j < n; j += blockDim.x) {
-            double t = 0.0;
-            for (int i = 0; i <= j; ++i) t += M[i * n + j] * w[i];
+            float t = 0.f;
+            for (int i = 0; i <= j; ++i) t += (float)M[i * n + j] * w[i];
             v[j] = t;
             t2 += t * t;
         }
-        lam = sqrt(block_sum(t2, red));    // |M^T M v| -> sigma_max^2
-        if (!(lam > 0.0) || !(lam < 1e300)) return lam;
+        lam = sqrtf(block_sum_f(t2, red));
+        if (!(lam > 0.f) || !(lam < 3e38f)) return lam;
         for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] /= lam;
         __syncthreads();
     }
-    return sqrt(lam);
+    return sqrtf(lam);
 }
 
 // z = X (X^T y) with X = R^{-1}: the solve (R^T R) z = y by two triangular matvecs
@@ -997,9 +1027,10 @@ __global__ void __launch_bounds__(FIT_THREADS) k_fit(FitParams P) {
                     if (S.X) {
                         tri_inverse(S.R, S.invd, S.X, ncol);
                         __syncthreads();
-                        double smax = block_sigma_max(S.R, ncol, S.vec, S.vec + ncm, S.scald + 8 - 4, 30);
-                        double sinv = block_sigma_max(S.X, ncol, S.vec, S.vec + ncm, S.scald + 8 - 4, 30);
-                        ratio = (smax > 0.0 && sinv > 0.0 && sinv < 1e300) ? 1.0 / (smax * sinv) : 0.0;
+                        float* fv = (float*)S.vec;          // 2 * ncm floats in vec[0 .. ncm)
+                        float smax = block_sigma_max(S.R, ncol, fv, fv + ncm, S.scald + 4, 30);
+                        float sinv = block_sigma_max(S.X, ncol, fv, fv + ncm, S.scald + 4, 30);
+                        ratio = (smax > 0.f && sinv > 0.f && sinv < 3e38f) ? 1.0 / ((double)smax * (double)sinv) : 0.0;
                     } else {
                         if (threadIdx.x < 32) {
                             double rr = warp_cond_ratio(S.R, S.invd, ncol, S.vec, S.vec + ncm);

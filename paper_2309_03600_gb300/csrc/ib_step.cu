@@ -19,7 +19,9 @@
 // Arithmetic: coefficients (dt^2 c^2 / h^2, dt rho c^2 / h, dt / (rho h)) are
 // formed in FP64 and rounded once; the leapfrog update is evaluated as
 // p + ((p - p_prev) + Kh * lap) to keep one rounding at the field's magnitude.
+#include <cuda.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
 #include <cmath>
@@ -322,6 +324,158 @@ __global__ void __launch_bounds__(256) k_leap3d(StepArgs<T> a, int zchunk, int64
         q[2 * H] = (col_ok && z + 1 < ze) ? a.p[L.idx(x, y, z + 1 + H)] : (T)0;
         __syncthreads();
     }
+}
+
+// ---------------------------------------------------------------------------
+// 3D leapfrog, FP32, with the plane tiles staged by TMA.  Each block marches a
+// 32 x 8 column tile through its z chunk.  Plane z (with an x halo of 4 -- the
+// 16-byte alignment of the box -- and a y halo of H) is fetched by one
+// cp.async.bulk.tensor into a ring of NS shared-memory slots, NS - H - 1 planes
+// ahead of use, each slot tracked by an mbarrier.  The z neighbours come from a
+// register queue fed by the centre of plane z + H.  Every wait is bounded: on
+// timeout the block records an error and leaves.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, int x, int y, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(smem_u32(dst)),
+        "l"(tm), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// bounded wait; returns false on timeout
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
+    for (int it = 0; it < (1 << 22); ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+
+template <int H>
+struct Tma3D {
+    static constexpr int TX = 32, TY = 8;
+    static constexpr int BW = TX + 8;         // x halo 4 on each side (16-byte aligned box)
+    static constexpr int BH = TY + 2 * H;
+    static constexpr int NS = H + 3;          // ring slots: planes z .. z + H + 2
+    static constexpr uint32_t BYTES = BW * BH * 4;
+    static constexpr int SLOT = (BW * BH + 31) / 32 * 32;   // slot stride in floats (128-byte multiple)
+};
+
+template <int H>
+__global__ void __launch_bounds__(256) k_leap3d_tma(StepArgs<float> a, const __grid_constant__ CUtensorMap tm,
+                                                    int zchunk, int64_t nty, int* err) {
+    using C = Tma3D<H>;
+    constexpr int TX = C::TX, TY = C::TY, BW = C::BW, NS = C::NS, SLOT = C::SLOT;
+    __shared__ alignas(128) float ring[NS * SLOT];
+    __shared__ alignas(8) uint64_t bar[NS];
+    __shared__ float acc[TY * TX];
+    __shared__ float sadd[TY * TX];
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * TX + tx;
+    const int64_t blk = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    record_receivers(a.rec, a.p, a.traces, a.nt, a.rec_step, blk * 256 + tid);
+    const Layout& L = a.L;
+    const int64_t x0 = (int64_t)blockIdx.x * TX, y0 = (int64_t)blockIdx.y * TY;
+    const int64_t x = x0 + tx, y = y0 + ty;
+    const int64_t zb = (int64_t)blockIdx.z * zchunk;
+    const int64_t ze = min(zb + zchunk, L.nz);
+    const int64_t zlast = ze - 1 + H;                 // last plane fetched by TMA
+    const bool col_ok = x < L.nx + H && y < L.ny + H;
+    const bool valid = x < L.nx && y < L.ny;
+    // tensor row of plane z, tile row y0 - H: (H + 1 + z) * py + y0
+    auto plane_row = [&](int64_t z) { return (int)((H + 1 + z) * L.py + y0); };
+    if (tid == 0) {
+        for (int i = 0; i < NS; ++i) mbar_init(&bar[i], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int i = 0; i < NS && zb + i <= zlast; ++i) {
+            mbar_expect_tx(&bar[i], C::BYTES);
+            tma_load_2d(&ring[i * SLOT], &tm, (int)(x0 - 4), plane_row(zb + i), &bar[i]);
+        }
+    }
+    float q[2 * H + 1];
+#pragma unroll
+    for (int k = 0; k < 2 * H; ++k) q[k] = col_ok ? a.p[L.idx(x, y, zb - H + k)] : 0.f;
+    const float wv = a.src.n ? a.wavelet[a.step] : 0.f;
+    int64_t qi = L.idx(x, y, zb);
+    float pm_n = valid ? a.pm[qi] : 0.f;
+    float kh_n = valid ? a.Kh[qi] : 0.f;
+    for (int64_t z = zb; z < ze; ++z) {
+        const int it = (int)(z - zb);
+        const int st = it % NS, sf = (it + H) % NS;
+        bool ok = mbar_wait_bounded(&bar[st], (uint32_t)((it / NS) & 1));
+        ok = ok && mbar_wait_bounded(&bar[sf], (uint32_t)(((it + H) / NS) & 1));
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) atomicExch(err, 1);
+            return;
+        }
+        // software pipeline: next plane's p_prev and Kh
+        const float pm_c = pm_n, kh_c = kh_n;
+        const int64_t qc = qi;
+        if (z + 1 < ze) {
+            qi += L.plane;
+            pm_n = valid ? a.pm[qi] : 0.f;
+            kh_n = valid ? a.Kh[qi] : 0.f;
+        }
+        const float* rt = ring + st * SLOT;          // plane z, row j <-> y0 - H + j
+        q[2 * H] = ring[sf * SLOT + (H + ty) * BW + 4 + tx];
+        sadd[tid] = 0.f;
+        {
+            const float c = q[H];
+            float sum = 0.f;
+#pragma unroll
+            for (int k = 1; k <= H; ++k)
+                sum += a.w2[k] * (((rt[(H + ty) * BW + 4 + tx + k] - c) + (rt[(H + ty) * BW + 4 + tx - k] - c)) +
+                                  ((rt[(H + ty + k) * BW + 4 + tx] - c) + (rt[(H + ty - k) * BW + 4 + tx] - c)) +
+                                  ((q[H + k] - c) + (q[H - k] - c)));
+            acc[tid] = sum;
+        }
+        const int64_t origin = L.idx(x0, y0, z);
+        __syncthreads();
+        tile_sources<float, TX, TY>(a.src, wv, origin, L.px, sadd, tid);
+        if (a.op.ptr) add_entries(a.op, (z * nty + blockIdx.y) * a.op.ntx + blockIdx.x, a.p, origin, acc, tid, 256);
+        __syncthreads();
+        if (valid) {
+            const float c = q[H];
+            a.out[qc] = c + ((c - pm_c) + kh_c * acc[tid]) + sadd[tid];
+        }
+#pragma unroll
+        for (int k = 0; k < 2 * H; ++k) q[k] = q[k + 1];
+        __syncthreads();
+        // slot st is free: fetch plane z + NS into it
+        if (tid == 0 && z + NS <= zlast) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(&bar[st], C::BYTES);
+            tma_load_2d(&ring[st * SLOT], &tm, (int)(x0 - 4), plane_row(z + NS), &bar[st]);
+        }
+    }
+    // planes fetched past the chunk that no iteration waited for (chunks shorter than H):
+    // complete them before the block leaves
+    bool ok = true;
+    for (int it = (int)(ze - zb); it <= (int)(zlast - zb); ++it)
+        ok = ok && mbar_wait_bounded(&bar[it % NS], (uint32_t)((it / NS) & 1));
+    if (!ok && tid == 0) atomicExch(err, 1);
 }
 
 // ---------------------------------------------------------------------------
@@ -689,6 +843,43 @@ static TileView<T> tview(const TileBins* b) {
 
 static const int TX2 = 64, TZ2 = 8;
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no libcuda link)
+static PFN_cuTensorMapEncodeTiled_v12000 tma_encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        cudaDriverEntryPointQueryResult q;
+        void* f = nullptr;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = (PFN_cuTensorMapEncodeTiled_v12000)f;
+    }
+    return fn;
+}
+
+static bool tma_enabled() {
+    const char* e = getenv("IB_NO_TMA");
+    return tma_encode_fn() != nullptr && !(e && e[0] == '1');
+}
+
+// 2D view of a padded FP32 3D field: rows of px elements; box (32 + 8) x (8 + 2H)
+static ib_status make_plane_map(CUtensorMap& tm, void* base, const Layout& L) {
+    cuuint64_t dims[2] = {(cuuint64_t)L.px, (cuuint64_t)(L.total / L.px)};
+    cuuint64_t strides[1] = {(cuuint64_t)L.px * 4};
+    cuuint32_t box[2] = {32 + 8, (cuuint32_t)(8 + 2 * L.H)};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = tma_encode_fn()(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
+                                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                 CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        ib_set_error("cuTensorMapEncodeTiled failed");
+        return IB_ERR_CUDA;
+    }
+    return IB_OK;
+}
+
 static ib_status check_shot(const ib_table* t, const ib_shot* sh, int precision, double dt, int nt,
                             bool need_traces = true) {
     if (!t || !sh) {
@@ -808,6 +999,15 @@ static ib_status forward_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, 
     const int zchunk = 32;
     dim3 grid3((unsigned)((L.nx + 31) / 32), (unsigned)((L.ny + 7) / 8), (unsigned)((L.nz + zchunk - 1) / zchunk));
     const int64_t nty3 = (L.ny + 7) / 8;
+    // FP32 3D: TMA-staged plane tiles (one tensor map per wavefield buffer)
+    CUtensorMap tmap[2];
+    int* err = nullptr;
+    const bool use_tma = d == 3 && sizeof(T) == 4 && tma_enabled();
+    if (use_tma) {
+        TRY(make_plane_map(tmap[0], (void*)p0, L));
+        TRY(make_plane_map(tmap[1], (void*)p1, L));
+        TRY(S.alloc(&err, 1, true));
+    }
     for (int n = 0; n < nt; ++n) {
         if (ckpt && n % seg == 0) {
             T* slot = (T*)ckpt + (int64_t)(n / seg) * 2 * L.total;
@@ -821,6 +1021,16 @@ static ib_status forward_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, 
         a.rec_step = n - 1;
         if (d == 2) {
             launch_leap2d<T>(a, H, grid2, s);
+        } else if (use_tma) {
+            dim3 blk(32, 8);
+            const CUtensorMap& tmc = (cur == p0) ? tmap[0] : tmap[1];
+            PROF_LAUNCH("leap3d_tma_f32", s, {
+                const StepArgs<float>& af = *reinterpret_cast<const StepArgs<float>*>(&a);
+                if (H == 1) k_leap3d_tma<1><<<grid3, blk, 0, s>>>(af, tmc, zchunk, nty3, err);
+                else if (H == 2) k_leap3d_tma<2><<<grid3, blk, 0, s>>>(af, tmc, zchunk, nty3, err);
+                else if (H == 3) k_leap3d_tma<3><<<grid3, blk, 0, s>>>(af, tmc, zchunk, nty3, err);
+                else k_leap3d_tma<4><<<grid3, blk, 0, s>>>(af, tmc, zchunk, nty3, err);
+            });
         } else {
             dim3 blk(32, 8);
             PROF_LAUNCH(kname<T>("leap3d_f32", "leap3d_f64"), s, {
@@ -837,6 +1047,15 @@ static ib_status forward_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, 
         k_receivers<T><<<grid1(g.rec.n, 256), 256, 0, s>>>(g.rec, cur, (T*)sh->traces_dev, nt, nt - 1);
         IB_CHECK_LAUNCH("k_receivers");
         ib_count_launch("setup");
+    }
+    if (use_tma) {
+        int herr = 0;
+        IB_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+        IB_CUDA(cudaStreamSynchronize(s));
+        if (herr) {
+            ib_set_error("a bounded TMA wait in the 3D step timed out");
+            return IB_ERR_TIMEOUT;
+        }
     }
     return IB_OK;
 }

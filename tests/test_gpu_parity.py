@@ -305,3 +305,27 @@ def test_forward_batch_matches_single_shots():
     w = shots[0]["w"]
     ref = sim.Leapfrog(w["sdf"], w["vel"], w["h"], w["M"], "free", dt, w["src"], w["rec"]).forward(w["wavelet"], 300)
     assert rel_l2(outs[0].double().cpu().numpy(), ref) < TOL32
+
+
+def test_forward_3d_tma_matches_plain_loads(monkeypatch):
+    """FP32 3D runs through the TMA-staged kernel by default; IB_NO_TMA=1 selects
+    the kernel with plain loads.  Both must give the same traces (nz = 34 also
+    leaves a z chunk shorter than the stencil half-width)."""
+    sdf, zs = small_hills()
+    h = 10.0
+    vel = np.full(sdf.shape, 1800.0)
+    dt = 0.4 * h / 1800.0
+    nt = 120
+    src = np.array([[20 * h, 17 * h, 26 * h]])
+    rec = np.array([[x * h, y * h, zs[y, x] + 2 * h] for x in range(4, 36, 5) for y in range(4, 32, 5)])
+    w = dict(sdf=sdf, vel=vel, h=h, M=8, dt=dt, nt=nt, src=src, rec=rec, wavelet=inputs.ricker(25.0, dt, nt))
+    monkeypatch.delenv("IB_NO_TMA", raising=False)
+    ib.ib_profile_enable(1)
+    tma = _run_leap(w, "free", torch.float32)
+    assert "leap3d_tma_f32" in ib.ib_profile()
+    monkeypatch.setenv("IB_NO_TMA", "1")
+    ib.ib_profile_enable(1)
+    plain = _run_leap(w, "free", torch.float32)
+    assert "leap3d_f32" in ib.ib_profile()
+    ib.ib_profile_enable(0)
+    assert rel_l2(tma, plain) < 1e-6
