@@ -176,7 +176,8 @@ def fit(xi0, fields, bps, bc_rows_fn, E, opts, lshape):
                 u[f * T:(f + 1) * T] += w * taylor.basis_row(np.asarray(xe, dtype=np.float64) - xi0, idx)
             y = np.linalg.pinv(A).T @ u
             info = dict(radius=r, order=Mp, n_bp=len(blist), n_rows=A.shape[0],
-                        n_int=len(sup), cond=float(sv[0] / sv[-1]), A=A, u=u, y=y)
+                        n_int=len(sup), cond=float(sv[0] / sv[-1]), A=A, u=u, y=y,
+                        support=[(f, j) for f, j, _ in sup])
             return [(f, j) for f, j, _ in sup], y[:len(sup)], info
     raise RankError("node at %s unconstrained" % (tuple(xi0),))
 
