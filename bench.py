@@ -23,6 +23,8 @@ import sys
 import threading
 import time
 
+import numpy as np
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -37,7 +39,10 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="stag2d",
-                    choices=["stag2d", "hills3d", "flat2d", "batch2d", "adjoint2d"])
+                    choices=["stag2d", "hills3d", "flat2d", "batch2d", "adjoint2d", "learned3d"])
+    ap.add_argument("--train-topos", type=int, default=24, help="learned3d: training topographies")
+    ap.add_argument("--epochs", type=int, default=8, help="learned3d: training epochs")
+    ap.add_argument("--accept-tol", type=float, default=1e-6, help="learned3d: exactness threshold")
     ap.add_argument("--nshot", type=int, default=48, help="shots of batch2d / adjoint2d")
     ap.add_argument("--bc", default="free", choices=["free", "rigid"])
     ap.add_argument("--nt", type=int, default=0, help="override time steps (testing only)")
@@ -297,6 +302,8 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
     if args.workload in ("batch2d", "adjoint2d"):
         return run_shots(args, world, rank, local, dev, dist)
+    if args.workload == "learned3d":
+        return run_learned(args, world, rank, local, dev, dist)
 
     w = make_workload(args.workload, args.bc, rank, args.nt, args.grid)
     dtype = torch.float64 if w["dtype"] == "f64" else torch.float32
@@ -426,6 +433,160 @@ def main():
                   "rank_failures": stats["n_rank_failures"], "boundary_points": stats["n_boundary_points"]},
         "roofline": roof, "kernels": kernels, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
         "gpu_launches": int(launches), "wall_s": wall,
+    }
+    print(json.dumps(out))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def train_network(args, dev, rank):
+    """Train the learned-stencil network on rows the plain constructor fits on
+    seeded training topographies (untimed; reported)."""
+    import torch
+    from paper_2309_03600_gb300 import ib, inputs
+    net = ib.Mlp(3, 8, n_hidden=256, n_layers=4)
+    net.set_params(inputs.mlp_init(net.n_in, 256, 4, net.n_out, seed=17))
+    Xs, Ts = [], []
+    t0 = time.perf_counter()
+    for k in range(args.train_topos):
+        sdf = torch.as_tensor(inputs.training_hills_sdf(1000 + k + 100000 * rank, device="cuda"),
+                              dtype=torch.float64, device=dev)
+        tab = ib.ib_build_stencils(sdf, 10.0, "free", "second", 8)
+        nodes, T = ib.ib_mlp_targets(tab, net)
+        Xs.append(ib.ib_mlp_features(net, sdf, 10.0, nodes, bc="free"))
+        Ts.append(T)
+        del tab, sdf
+    X, T = torch.cat(Xs), torch.cat(Ts)
+    del Xs, Ts
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    g = torch.Generator(device=dev).manual_seed(0)
+    B = 4096
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    n_steps = 0
+    loss = None
+    first = None
+    for ep in range(args.epochs):
+        perm = torch.randperm(X.shape[0], device=dev, generator=g)
+        for b in range(0, X.shape[0] - B + 1, B):
+            loss = ib.ib_mlp_train_step(net, X, T, perm[b:b + B], lr=1e-3 if ep < args.epochs - 2 else 3e-4)
+            if first is None:
+                first = float(loss.item())
+            n_steps += 1
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    info = {"rows": int(X.shape[0]), "topographies": args.train_topos, "epochs": args.epochs,
+            "batch": B, "steps": n_steps, "data_seconds": t_data, "train_ms": ms,
+            "samples_per_s": n_steps * B / (ms * 1e-3), "first_loss": first,
+            "final_loss": float(loss.item()) if loss is not None else None}
+    del X, T
+    return net, info
+
+
+def run_learned(args, world, rank, local, dev, dist):
+    """learned3d: the network proposes each IB row, the exactness test keeps or
+    rejects it, rejected rows are fitted; then 1500 FP32 steps.  One step =
+    ib_build_stencils_learned + ib_forward on the 768 x 768 x 384 model."""
+    import torch
+    from paper_2309_03600_gb300 import ib, inputs
+    net, train = train_network(args, dev, rank)
+    kw = {}
+    if args.grid:
+        kw = dict(nx=args.grid[0], ny=args.grid[1], nz=args.grid[2])
+    w = inputs.workload_learned3d(seed=5 + 1000 * rank, device="cuda", **kw)
+    nt = args.nt or w["nt"]
+    sdf = torch.as_tensor(w["sdf"], dtype=torch.float64, device=dev)
+    vel = torch.as_tensor(w["vel"], dtype=torch.float32, device=dev)
+    wav = torch.as_tensor(w["wavelet"][:nt], dtype=torch.float32, device=dev)
+    src = torch.as_tensor(w["src"], dtype=torch.float64, device=dev)
+    rec = torch.as_tensor(w["rec"], dtype=torch.float64, device=dev)
+    traces = torch.zeros((rec.shape[0], nt), dtype=torch.float32, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    N = grid_points(w)
+
+    def step():
+        t = ib.ib_build_stencils_learned(sdf, w["h"], net, space_order=8, accept_tol=args.accept_tol)
+        ib.ib_forward(t, vel, wav, src, rec, w["dt"], nt, traces=traces)
+        return t
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        tab = step()
+    torch.cuda.synchronize()
+    clocks = Clocks(local)
+    ib.ib_profile_enable(8)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        tab = step()
+        e1.record(stream)
+        ev.append((e0, e1))
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    prof = ib.ib_profile()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
+    if dist:
+        tt = torch.tensor([ms], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ms = float(tt.item())
+    st = tab.stats()
+    checked, accepted, res = ib.ib_table_learned(tab)
+    fin = res[np.isfinite(res)] if res.size else res
+    # the same geometry through the plain constructor, for comparison
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    plain = ib.ib_build_stencils(sdf, w["h"], "free", "second", 8)
+    torch.cuda.synchronize()
+    t_plain = time.perf_counter() - t0
+    kernels = {k: {"launches": d["launches"], "avg_us": 1e3 * d["sampled_ms"] / d["sampled"]}
+               for k, d in prof.items() if d["sampled"]}
+    peak, peak_kind = peaks()
+    roof = None
+    kb = kernel_bytes(w, st, 4)
+    for name in ("leap3d_tma_f32", "leap3d_f32"):
+        d = prof.get(name)
+        if d and d["sampled"]:
+            avg_s = d["sampled_ms"] / d["sampled"] * 1e-3
+            ach = kb[name] / avg_s / 1e9
+            roof = {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peak, "peak_kind": peak_kind,
+                    "unit": "GB/s", "frac": ach / peak, "traffic": dram_traffic(name),
+                    "algorithmic_bytes_per_launch": kb[name], "avg_launch_us": avg_s * 1e6,
+                    "frac_of_nominal_8TBs": ach / 8000.0}
+            break
+    if rank != 0:
+        return 0
+    out = {
+        "metric": METRIC, "value": world * N * nt / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "learned3d", "desc": "3D second-order, %dx%dx%d, h=10 m, order 8, FP32, %d steps, "
+                   "60 Gaussian hills free surface; rows proposed by the MLP (4x256, bf16) and kept if the "
+                   "exactness residual <= %g" % (w["shape"][0], w["shape"][1], w["shape"][2], nt, args.accept_tol),
+                   "grid": list(w["shape"]), "nt": nt, "l2": "flushed between steps (256 MB write)"},
+        "setup": {"learned_seconds": st["setup_seconds"], "plain_seconds": t_plain,
+                  "ib_rows": st["rows"][0], "rows_checked": checked, "rows_accepted": accepted,
+                  "residual_median": float(np.median(fin)) if fin.size else None,
+                  "residual_p10": float(np.percentile(fin, 10)) if fin.size else None,
+                  "rows_below_1e-4": int((fin <= 1e-4).sum()), "rows_below_1e-2": int((fin <= 1e-2).sum()),
+                  "ib_rows_per_s_learned": st["rows"][0] / max(st["setup_seconds"], 1e-9),
+                  "ib_rows_per_s_plain": st["rows"][0] / max(t_plain, 1e-9)},
+        "training": train,
+        "roofline": roof, "kernels": kernels, "e2e": None, "cpu_baseline": None, "clocks": clk,
+        "gpu_launches": int(sum(d["launches"] for d in prof.values())),
     }
     print(json.dumps(out))
     if dist:

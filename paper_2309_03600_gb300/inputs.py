@@ -283,13 +283,13 @@ def workload_sinusoid_staggered(nx=1001, nz=1001, h=5.0, M=8, nt=3000, courant=0
 
 
 def workload_hills3d(nx=512, ny=512, nz=384, h=10.0, M=8, nt=2000, courant=0.45, seed=3,
-                     n_hills=12, f0=10.0, bc="free", rec_stride=2, device="cpu"):
+                     n_hills=12, f0=10.0, bc="free", rec_stride=2, device="cpu", hmax=400.0):
     """3D second-order: z_s = 1000 m - sum of seeded Gaussian hills (heights
     50-400 m, widths 300-1500 m), clamped at 100 m; smooth random velocity in
     [1500, 4000] m/s increasing with depth; 10 Hz source 500 m below the
     surface at the centre; receivers every `rec_stride` nodes 2 h below it."""
     Lx, Ly = (nx - 1) * h, (ny - 1) * h
-    prm = hills_params(n_hills, seed, Lx, Ly)
+    prm = hills_params(n_hills, seed, Lx, Ly, hmax=hmax)
     parts = hills_surface(prm)
     sdf, zsurf = heightfield_sdf_3d(nx, ny, nz, h, parts, device=device)
     vel = smooth_random_velocity_3d(nx, ny, nz, h, zsurf, seed, device=device)
@@ -337,3 +337,52 @@ def workload_shot2d(shot, h=10.0, M=8, nt=2000, courant=0.4, f0=10.0, bc="free",
     rec = np.stack([rx, rz], axis=1)
     return dict(name="shot2d_%d" % shot, ndim=2, shape=(nx, nz), h=h, M=M, sdf=sdf, vel=vel,
                 dt=dt, nt=nt, src=src, rec=rec, wavelet=ricker(f0, dt, nt), bc=bc)
+
+
+# ---------------------------------------------------------------------------
+# learned-stencil network: seeded initial parameters and training topographies
+# ---------------------------------------------------------------------------
+def mlp_init(n_in, n_hidden, n_layers, n_out, seed):
+    """Flat FP32 parameter vector (W_0, b_0, W_1, b_1, ...), W_l [n_out][n_in]
+    uniform in +-sqrt(6 / fan_in) (He initialisation), biases zero."""
+    rng = np.random.default_rng(seed)
+    dims = [n_in] + [n_hidden] * n_layers + [n_out]
+    parts = []
+    for i in range(len(dims) - 1):
+        a = math.sqrt(6.0 / dims[i])
+        parts.append(rng.uniform(-a, a, size=dims[i + 1] * dims[i]))
+        parts.append(np.zeros(dims[i + 1]))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def random_hills_sdf(nx, ny, nz, h, seed, n_hills=12, device="cpu"):
+    """SDF of a seeded sum of Gaussian hills on a datum at ~55% depth, with
+    heights and widths scaled to the grid (training topographies)."""
+    rng = np.random.default_rng(seed + 7919)
+    depth = (nz - 1) * h
+    prm = hills_params(n_hills, seed, (nx - 1) * h, (ny - 1) * h, hmin=0.05 * depth, hmax=0.3 * depth,
+                       smin=3.0 * h, smax=0.2 * min(nx, ny) * h)
+    datum = float(rng.uniform(0.5, 0.6)) * depth
+    parts = hills_surface(prm, datum=datum, zmin=0.15 * depth)
+    sdf, _ = heightfield_sdf_3d(nx, ny, nz, h, parts, device=device)
+    return sdf
+
+
+def workload_learned3d(nx=768, ny=768, nz=384, h=10.0, M=8, nt=1500, seed=5, device="cpu"):
+    """3D second-order on a sum of 60 seeded Gaussian hills (heights 50-250 m,
+    widths 300-1500 m) on a 1 km datum, free surface, order 8, 1500 steps;
+    receivers every third node 2 h below the surface."""
+    w = workload_hills3d(nx=nx, ny=ny, nz=nz, h=h, M=M, nt=nt, seed=seed, n_hills=60, hmax=250.0,
+                         rec_stride=3, device=device)
+    w["name"] = "learned3d"
+    return w
+
+
+def training_hills_sdf(seed, nx=256, ny=256, nz=160, h=10.0, device="cpu"):
+    """Training topography for the learned stencils: the same hill statistics
+    as ``workload_learned3d`` (7 hills on a 256 x 256 patch), seeded."""
+    Lx, Ly = (nx - 1) * h, (ny - 1) * h
+    prm = hills_params(7, seed, Lx, Ly, hmax=250.0)
+    parts = hills_surface(prm, datum=0.6 * (nz - 1) * h, zmin=0.2 * (nz - 1) * h)
+    sdf, _ = heightfield_sdf_3d(nx, ny, nz, h, parts, device=device)
+    return sdf
