@@ -498,6 +498,7 @@ def run_learned(args, world, rank, local, dev, dist):
     if args.grid:
         kw = dict(nx=args.grid[0], ny=args.grid[1], nz=args.grid[2])
     w = inputs.workload_learned3d(seed=5 + 1000 * rank, device="cuda", **kw)
+    w["form"] = "second"
     nt = args.nt or w["nt"]
     sdf = torch.as_tensor(w["sdf"], dtype=torch.float64, device=dev)
     vel = torch.as_tensor(w["vel"], dtype=torch.float32, device=dev)

@@ -235,6 +235,116 @@ ib_status ib_forward_batch(const ib_table* const* tables, const ib_shot* shots,
 ib_status ib_forward_noalloc(const ib_table* table, const ib_shot* shot, double dt,
                              int32_t nt, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Learned modified stencils.  The paper builds every modified row by its
+ * constrained least-squares fit ("Reconciliation with the Interior Numerical
+ * Discretization"); it has no learned component.  These entry points add a
+ * predictor on top of the method without changing it: a multilayer
+ * perceptron maps the signed distance around an IB row's node to the row's
+ * correction weights, and a prediction is kept only if it passes the
+ * exactness test the fit itself guarantees; every other row is fitted as in
+ * ib_build_stencils.  Second-order (Laplacian) rows only.
+ * ------------------------------------------------------------------------ */
+typedef struct ib_mlp ib_mlp;        /* opaque, library-owned */
+
+typedef struct {
+    int32_t ndim;          /* 2 or 3                                           */
+    int32_t space_order;   /* M of the rows it predicts (even, 2..8)           */
+    int32_t n_hidden;      /* width of every hidden layer, 8..1024, multiple of 8 */
+    int32_t n_layers;      /* hidden layers, 1..8                              */
+    double in_radius;      /* inputs: SDF / h at lattice offsets |o| <= in_radius
+                              around the row node (nearest in-array node past
+                              the array edge), then [free, rigid, M / 8]       */
+    double out_radius;     /* outputs: corrections at offsets |o| <= out_radius,
+                              which must equal the first support radius of the
+                              fit, (min(M, basis order) + 1) / 2 by default    */
+} ib_mlp_config;
+
+/*
+ * ib_mlp_create -- network on the current device with zeroed parameters.
+ * Offsets are ordered by distance, then by array order (z, y, x), as the
+ * fit orders its support.  Layers: Linear -> ReLU for each hidden layer, then
+ * Linear.  Weights W_l are [n_out_l][n_in_l] row-major, FP32 masters in one
+ * flat vector (W_0, b_0, W_1, b_1, ...); the products use bfloat16 copies of
+ * the weights and activations with FP32 accumulation.
+ * Errors: IB_ERR_ARG (config out of range), IB_ERR_OOM, IB_ERR_CUDA.
+ */
+ib_status ib_mlp_create(const ib_mlp_config* cfg, ib_mlp** out);
+void ib_mlp_free(ib_mlp* mlp);
+
+/* Sizes: inputs per row, outputs per row, parameters. */
+ib_status ib_mlp_info(const ib_mlp* mlp, int64_t* n_in, int64_t* n_out, int64_t* n_params);
+
+/*
+ * ib_mlp_buffers -- library-owned device vectors of n_params FP32 values:
+ * parameters, last gradient, Adam first and second moments.  Any may be NULL.
+ * After writing parameters directly call ib_mlp_sync_weights.
+ */
+ib_status ib_mlp_buffers(ib_mlp* mlp, float** params, float** grads, float** adam_m, float** adam_v);
+ib_status ib_mlp_sync_weights(ib_mlp* mlp, void* stream);
+
+/*
+ * ib_mlp_features -- inputs of n rows: X[i][*] (bfloat16, n_in per row) for
+ * the node with linear index nodes_dev[i] (x fastest) of the grid whose FP64
+ * SDF is sdf_dev.  Errors: IB_ERR_ARG (ndim differs from the config).
+ */
+ib_status ib_mlp_features(const ib_mlp* mlp, const ib_grid* grid, const double* sdf_dev,
+                          const int64_t* nodes_dev, int64_t n, ib_bc bc, void* X_dev, void* stream);
+
+/* ib_mlp_forward -- Y[n][n_out] (FP32) = network(X[n][n_in] bfloat16). */
+ib_status ib_mlp_forward(ib_mlp* mlp, const void* X_dev, int64_t n, float* Y_dev, void* stream);
+
+/*
+ * ib_mlp_train_step -- one Adam step (Kingma & Ba) on the mean over rows and
+ * outputs of (Y - T)^2 for the minibatch rows idx_dev[0..n) of X (bfloat16
+ * [*][n_in]) and T (FP32 [*][n_out]).  The gradient is left in the grads
+ * buffer; *loss_dev (device FP32) receives the minibatch loss before the
+ * step.  Scratch grows with n and is kept.  Errors: IB_ERR_ARG, IB_ERR_OOM.
+ */
+ib_status ib_mlp_train_step(ib_mlp* mlp, const void* X_dev, const float* T_dev,
+                            const int64_t* idx_dev, int64_t n, float lr, float beta1,
+                            float beta2, float eps, float* loss_dev, void* stream);
+
+/*
+ * ib_mlp_targets -- training rows from a table built by ib_build_stencils
+ * (second-order form): the Laplacian rows fitted at the first support radius
+ * and full basis order whose entries all lie on the output footprint.
+ * Writes their node indices (nodes_dev, int64) and correction weights in grid
+ * units on the footprint (T_dev, FP32 [*][n_out]), at most cap rows, and
+ * their count to *n_rows (host).  Synchronises the stream.
+ */
+ib_status ib_mlp_targets(const ib_table* table, const ib_mlp* mlp, int64_t* nodes_dev,
+                         float* T_dev, int64_t cap, int64_t* n_rows, void* stream);
+
+/*
+ * ib_build_stencils_learned -- ib_build_stencils (second-order form) in
+ * which each IB row first takes the network's prediction and keeps it if its
+ * exactness residual is at most accept_tol; the residual is
+ * |N^T (A_I^T c - u)| / |u| with A_I the fit's interior rows at the first
+ * support radius, u = sum_e w_e a(x_e - x0) and N an orthonormal basis of the
+ * null space of the fit's boundary-condition rows (rank threshold 1e-10 of
+ * the largest row norm after QR): zero iff the row is exact on every basis
+ * polynomial that satisfies the boundary conditions.  Rows whose BC rows
+ * have full column rank (no such polynomial: the test would pass vacuously)
+ * are not checked.  Rejected and unchecked rows (and rows whose support
+ * leaves the footprint) are fitted as in
+ * ib_build_stencils, so accept_tol < 0 reproduces its table.
+ * Errors: those of ib_build_stencils; IB_ERR_ARG if the form is not
+ * second order or the config does not match the grid and options.
+ */
+ib_status ib_build_stencils_learned(const ib_grid* grid, const double* sdf_dev, ib_bc bc,
+                                    const ib_opts* opts, ib_mlp* mlp, double accept_tol,
+                                    ib_table** out, void* stream);
+
+/*
+ * ib_table_learned -- rows checked against and accepted from the network in
+ * ib_build_stencils_learned; resid_host (nullable, [rows of op 0]) receives
+ * each row's residual (+inf where the prediction was not applicable, NaN
+ * where the table was built without a network).
+ */
+ib_status ib_table_learned(const ib_table* table, int64_t* n_checked, int64_t* n_accepted,
+                           double* resid_host);
+
 /*
  * Measurement hooks (no counterpart in the paper).  ib_profile_enable(stride)
  * resets the per-kernel counters; with stride > 0 every stride-th launch of

@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libibwave.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["ib_build.cu", "ib_step.cu", "ib_prof.cu"]
+SOURCES = ["ib_build.cu", "ib_step.cu", "ib_prof.cu", "ib_mlp.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -497,6 +497,14 @@ struct FitParams {
     double* pool_w;
     unsigned long long* pool_top;
     int64_t pool_cap;
+    // learned rows (pred == nullptr: plain fit only)
+    const float* pred;          // [nrows][n_out] predicted corrections on the footprint
+    int n_out;
+    const int32_t* fp_lut;      // footprint index of offset (dx, dy, dz) in [-R, R]^3, or -1
+    int fp_R;
+    double accept_tol;
+    double* resid;              // [nrows] exactness residual of the prediction
+    uint8_t* accepted;          // [nrows]
 };
 
 __constant__ double c_inv_int[10] = {0.0, 1.0, 0.5, 1.0 / 3.0, 0.25, 0.2, 1.0 / 6.0, 1.0 / 7.0, 0.125, 1.0 / 9.0};
@@ -837,6 +845,170 @@ __device__ void x_solve(const double* X, int n, const double* y, double* t, doub
     __syncthreads();
 }
 
+// right-hand side u = sum_e w_e a(x_e - x0) over the exterior stencil points
+__device__ void fit_rhs(const FitParams& P, const OrderDesc& od, unsigned emask, int ncol, double* u) {
+    for (int col = threadIdx.x; col < ncol; col += blockDim.x) {
+        int f = col / od.T;
+        int k = col - f * od.T;
+        double acc = 0.0;
+        for (int e = 0; e < P.rule.nE; ++e) {
+            if (!((emask >> e) & 1u)) continue;
+            int ef = P.rule.Efield[e];
+            int fi = 0;   // unknown field index of this stencil point's field kind
+            for (int ff = 0; ff < P.nf; ++ff)
+                if (P.fkind[ff] == ef) fi = ff;
+            if (fi != f) continue;
+            double d[3], pw[3 * PW];
+            for (int a = 0; a < 3; ++a)
+                d[a] = a < P.g.ndim ? 0.5 * (double)(2 * P.rule.Eoff[e][a] + P.fshift2[f][a] - P.x0shift2[a]) : 0.0;
+            power_table(d, pw);
+            acc += P.rule.Ew[e] * mono_pw(pw, od.K + 3 * k, nullptr);
+        }
+        u[col] = acc;
+    }
+}
+
+// reserve n pool entries (whole block); false on overflow
+__device__ bool pool_alloc(const FitParams& P, const FitSmem& S, int n, int64_t* start) {
+    if (threadIdx.x == 0) {
+        unsigned long long st = atomicAdd(P.pool_top, (unsigned long long)n);
+        S.scal[1] = (int)(st & 0x7fffffff);
+        S.scal[2] = (int)(st >> 31);
+    }
+    __syncthreads();
+    *start = ((int64_t)S.scal[2] << 31) | (int64_t)S.scal[1];
+    __syncthreads();
+    return *start + n <= P.pool_cap;
+}
+
+__device__ __forceinline__ int fp_index(const FitParams& P, int32_t code) {
+    int dx, dy, dz;
+    unpack_off(code & 0xffffff, dx, dy, dz);
+    const int R = P.fp_R, W = 2 * R + 1;
+    if (dx < -R || dx > R || dy < -R || dy > R || dz < -R || dz > R) return -1;
+    return P.fp_lut[((dz + R) * W + (dy + R)) * W + (dx + R)];
+}
+
+// Exactness residual of the predicted correction of this row at the current
+// support: v = A_I^T c - u, projected on the null space of the BC rows (the
+// orthogonal complement of the row space of R_B, A_B = Q_B R_B), relative to
+// |u|.  The row space is spanned by classical Gram-Schmidt with one
+// re-orthogonalisation over the rows of R_B, dropping rows whose remainder is
+// below 1e-10 of the largest row norm.  +inf when the prediction does not
+// apply (a support node off the footprint, coupled fields, too many columns)
+// or cannot be checked (the BC rows have full column rank, so no basis
+// polynomial satisfies them and exactness says nothing).
+__device__ double learned_residual(const FitParams& P, const OrderDesc& od, const FitSmem& S, int64_t row,
+                                   int nsup, int nbcrow, int m, int ncol, unsigned emask) {
+    const int ncm = P.ncol_max;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+    if (threadIdx.x == 0) S.scal[4] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < nsup; i += blockDim.x)
+        if (fp_index(P, S.sup[i]) < 0) S.scal[4] = 1;
+    __syncthreads();
+    if (S.scal[4] != 0 || S.X == nullptr || P.nf != 1) return INFINITY;
+    double* u = S.vec;
+    double* v = S.vec + ncm;
+    double* w = S.vec + 2 * ncm;
+    double* dots = S.vec + 3 * ncm;
+    double* rn = S.invd;                  // row norms^2 of R_B
+    double* red = S.scald + 4;
+    fit_rhs(P, od, emask, ncol, u);
+    __syncthreads();
+    for (int col = threadIdx.x; col < ncol; col += blockDim.x) v[col] = -u[col];
+    // v += A_I^T c
+    double* ci = S.scald + 16;            // [FIT_PB]
+    for (int row0 = 0; row0 < nsup; row0 += FIT_PB) {
+        build_panel(P, od, S, nsup, nbcrow, nsup, row0, ncol);
+        for (int i = threadIdx.x; i < FIT_PB; i += blockDim.x)
+            ci[i] = row0 + i < nsup ? (double)P.pred[row * P.n_out + fp_index(P, S.sup[row0 + i])] : 0.0;
+        __syncthreads();
+        for (int col = threadIdx.x; col < ncol; col += blockDim.x) {
+            double a = 0.0;
+            for (int i = 0; i < FIT_PB; ++i) a += S.B[i * ncol + col] * ci[i];
+            v[col] += a;
+        }
+        __syncthreads();
+    }
+    // R_B: streamed QR of the boundary-condition rows only
+    for (int i = threadIdx.x; i < ncol * ncol; i += blockDim.x) S.R[i] = 0.0;
+    __syncthreads();
+    for (int row0 = nsup; row0 < m; row0 += FIT_PB) {
+        build_panel(P, od, S, nsup, nbcrow, m, row0, ncol);
+        __syncthreads();
+        qr_panel(S, ncol);
+    }
+    for (int i = warp; i < ncol; i += nwarp) {
+        double a = 0.0;
+        for (int j = lane; j < ncol; j += 32) a += S.R[i * ncol + j] * S.R[i * ncol + j];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        if (lane == 0) rn[i] = a;
+    }
+    __syncthreads();
+    double rmax2 = 0.0;
+    for (int i = 0; i < ncol; ++i) rmax2 = fmax(rmax2, rn[i]);
+    const double thr2 = 1e-20 * rmax2;
+    double* X = S.X;                      // orthonormal rows
+    int nq = 0;
+    for (int i = 0; i < ncol; ++i) {
+        if (!(rn[i] > thr2)) continue;
+        for (int j = threadIdx.x; j < ncol; j += blockDim.x) w[j] = S.R[i * ncol + j];
+        __syncthreads();
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int q = warp; q < nq; q += nwarp) {
+                double a = 0.0;
+                for (int j = lane; j < ncol; j += 32) a += X[q * ncol + j] * w[j];
+                for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+                if (lane == 0) dots[q] = a;
+            }
+            __syncthreads();
+            for (int j = threadIdx.x; j < ncol; j += blockDim.x) {
+                double a = w[j];
+                for (int q = 0; q < nq; ++q) a -= dots[q] * X[q * ncol + j];
+                w[j] = a;
+            }
+            __syncthreads();
+        }
+        double part = 0.0;
+        for (int j = threadIdx.x; j < ncol; j += blockDim.x) part += w[j] * w[j];
+        const double n2 = block_sum(part, red);
+        if (n2 > thr2) {
+            const double inv = 1.0 / sqrt(n2);
+            for (int j = threadIdx.x; j < ncol; j += blockDim.x) X[nq * ncol + j] = w[j] * inv;
+            ++nq;
+        }
+        __syncthreads();
+    }
+    // no polynomial of the basis satisfies every boundary condition: the test
+    // has no content, so the prediction cannot be verified
+    if (nq >= ncol) return INFINITY;
+    // remove the row-space part of v (twice)
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int q = warp; q < nq; q += nwarp) {
+            double a = 0.0;
+            for (int j = lane; j < ncol; j += 32) a += X[q * ncol + j] * v[j];
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            if (lane == 0) dots[q] = a;
+        }
+        __syncthreads();
+        for (int j = threadIdx.x; j < ncol; j += blockDim.x) {
+            double a = v[j];
+            for (int q = 0; q < nq; ++q) a -= dots[q] * X[q * ncol + j];
+            v[j] = a;
+        }
+        __syncthreads();
+    }
+    double pv = 0.0, pu = 0.0;
+    for (int j = threadIdx.x; j < ncol; j += blockDim.x) {
+        pv += v[j] * v[j];
+        pu += u[j] * u[j];
+    }
+    const double nv2 = block_sum(pv, red);
+    const double nu2 = block_sum(pu, red);
+    return sqrt(nv2) / (nu2 > 0.0 ? sqrt(nu2) : 1.0);
+}
+
 __global__ void __launch_bounds__(FIT_THREADS) k_fit(FitParams P) {
     extern __shared__ double smem_d[];
     const int ncm = P.ncol_max;
@@ -1002,6 +1174,36 @@ __global__ void __launch_bounds__(FIT_THREADS) k_fit(FitParams P) {
                 }
                 const int nbcrow = od.nbc;
                 const int m = nsup + nbp * nbcrow;
+                if (P.pred && oi == 0 && gstep == 0) {
+                    // ---- learned row: keep the prediction if it is exact on the BC-satisfying basis
+                    const double rho = learned_residual(P, od, S, row, nsup, nbcrow, m, ncol, emask);
+                    if (threadIdx.x == 0) P.resid[row] = rho;
+                    if (rho <= P.accept_tol && rho < INFINITY) {
+                        int64_t start;
+                        if (!pool_alloc(P, S, nsup, &start)) {
+                            status = 3;
+                            done = true;
+                            break;
+                        }
+                        for (int i = threadIdx.x; i < nsup; i += blockDim.x) {
+                            P.pool_code[start + i] = S.sup[i] & 0xffffff;
+                            P.pool_field[start + i] = (int8_t)(S.sup[i] >> 24);
+                            P.pool_w[start + i] = (double)P.pred[row * P.n_out + fp_index(P, S.sup[i])];
+                        }
+                        if (threadIdx.x == 0) {
+                            P.start[row] = start;
+                            P.accepted[row] = 1;
+                        }
+                        status = 0;
+                        used_order = od.order;
+                        used_r2 = (int)lrint(2.0 * r);
+                        used_nbp = nbp;
+                        nsup_final = nsup;
+                        done = true;
+                        break;
+                    }
+                    __syncthreads();
+                }
                 if (m < ncol) continue;
                 // ---- streamed Householder QR
                 for (int i = threadIdx.x; i < ncol * ncol; i += blockDim.x) S.R[i] = 0.0;
@@ -1047,26 +1249,9 @@ __global__ void __launch_bounds__(FIT_THREADS) k_fit(FitParams P) {
                 double* z = S.vec + ncm;        // [ncol]
                 double* rho = S.vec + 2 * ncm;  // [ncol]
                 double* tv = S.vec + 3 * ncm;   // [ncol] scratch
-                for (int col = threadIdx.x; col < ncol; col += blockDim.x) {
-                    int f = col / od.T;
-                    int k = col - f * od.T;
-                    double acc = 0.0;
-                    for (int e = 0; e < P.rule.nE; ++e) {
-                        if (!((emask >> e) & 1u)) continue;
-                        int ef = P.rule.Efield[e];
-                        int fi = 0;   // unknown field index of this stencil point's field kind
-                        for (int ff = 0; ff < P.nf; ++ff)
-                            if (P.fkind[ff] == ef) fi = ff;
-                        if (fi != f) continue;
-                        double d[3], pw[3 * PW];
-                        for (int a = 0; a < 3; ++a)
-                            d[a] = a < P.g.ndim ? 0.5 * (double)(2 * P.rule.Eoff[e][a] + P.fshift2[f][a] - P.x0shift2[a]) : 0.0;
-                        power_table(d, pw);
-                        acc += P.rule.Ew[e] * mono_pw(pw, od.K + 3 * k, nullptr);
-                    }
-                    u[col] = acc;
-                    z[col] = acc;
-                }
+                fit_rhs(P, od, emask, ncol, u);
+                __syncthreads();
+                for (int col = threadIdx.x; col < ncol; col += blockDim.x) z[col] = u[col];
                 __syncthreads();
                 if (S.X) {
                     x_solve(S.X, ncol, u, tv, z);
@@ -1111,14 +1296,8 @@ __global__ void __launch_bounds__(FIT_THREADS) k_fit(FitParams P) {
                 }
                 __syncthreads();
                 // ---- output: y_i = A_i z for interior rows
-                if (threadIdx.x == 0) {
-                    unsigned long long st = atomicAdd(P.pool_top, (unsigned long long)nsup);
-                    S.scal[1] = (int)(st & 0x7fffffff);
-                    S.scal[2] = (int)(st >> 31);
-                }
-                __syncthreads();
-                int64_t start = ((int64_t)S.scal[2] << 31) | (int64_t)S.scal[1];
-                if (start + nsup > P.pool_cap) {
+                int64_t start;
+                if (!pool_alloc(P, S, nsup, &start)) {
                     status = 3;   // pool overflow: re-run with a larger pool
                     done = true;
                     break;
@@ -1279,6 +1458,10 @@ static ib_status compact(const uint8_t* flags, int64_t n, int64_t** out, int64_t
     return IB_OK;
 }
 
+ib_status ib_compact(const uint8_t* flags, int64_t n, int64_t** out, int64_t* count, cudaStream_t s) {
+    return compact(flags, n, out, count, s);
+}
+
 static ib_status excl_scan(const int64_t* in, int64_t* out, int64_t n, cudaStream_t s) {
     size_t tmp = 0;
     IB_CUDA(cub::DeviceScan::ExclusiveSum(nullptr, tmp, in, out, n, s));
@@ -1354,6 +1537,11 @@ struct FitKind {
     double feta[3];
     int x0shift2[3];
     bool vector_bc;
+    // learned rows (second-order form): network, the geometry it reads, acceptance threshold
+    ib_mlp* mlp = nullptr;
+    const ib_grid* grid = nullptr;
+    const double* sdf = nullptr;
+    double accept_tol = -1.0;
 };
 
 // Build the fits of one kind and return the packed per-field CSR tables.
@@ -1452,6 +1640,29 @@ static ib_status run_fit(ib_table* t, const Geo& g, const FitKind& fk, const int
         P.ball_q[f] = dq;
         P.nball[f] = (int)q.size();
     }
+    // learned predictions of every row (checked inside k_fit)
+    uint8_t* accepted = nullptr;
+    if (fk.mlp) {
+        if (fk.nf != 1 || P.ncol_max > 64 || fabs(P.ord[0].r0 - ib_mlp_out_radius(fk.mlp)) > 1e-12) {
+            ib_set_error("learned stencils: the network's output radius must equal the first support radius "
+                         "of a single-field fit with at most 64 columns");
+            return IB_ERR_ARG;
+        }
+        TRY(dalloc(&t->learned_resid, std::max<int64_t>(nrows, 1)));
+        t->learned_rows = nrows;
+        IB_CUDA(cudaMemsetAsync(t->learned_resid, 0xff, sizeof(double) * std::max<int64_t>(nrows, 1), s));
+        TRY(tmp.alloc(&accepted, std::max<int64_t>(nrows, 1)));
+        float* pred = nullptr;
+        const int n_out = ib_mlp_out_count(fk.mlp);
+        TRY(tmp.alloc(&pred, std::max<int64_t>(nrows, 1) * n_out));
+        if (nrows) TRY(ib_mlp_predict_nodes(fk.mlp, fk.grid, fk.sdf, rows, nrows, t->bc, pred, s));
+        P.pred = pred;
+        P.n_out = n_out;
+        P.fp_lut = ib_mlp_lut(fk.mlp, &P.fp_R);
+        P.accept_tol = fk.accept_tol;
+        P.resid = t->learned_resid;
+        P.accepted = accepted;
+    }
     // outputs
     int32_t *info, *cnt;
     int64_t* start;
@@ -1471,6 +1682,7 @@ static ib_status run_fit(ib_table* t, const Geo& g, const FitKind& fk, const int
         TRY(tmp.alloc(&pool_field, cap));
         TRY(tmp.alloc(&pool_w, cap));
         IB_CUDA(cudaMemsetAsync(top, 0, sizeof(unsigned long long), s));
+        if (accepted) IB_CUDA(cudaMemsetAsync(accepted, 0, std::max<int64_t>(nrows, 1), s));
         P.rows = rows;
         P.nrows = nrows;
         P.info = info;
@@ -1514,6 +1726,16 @@ static ib_status run_fit(ib_table* t, const Geo& g, const FitKind& fk, const int
         }
     }
     t->n_fail += nfail;
+    if (accepted && nrows) {
+        std::vector<uint8_t> hacc(nrows);
+        std::vector<double> hres(nrows);
+        IB_CUDA(cudaMemcpy(hacc.data(), accepted, nrows, cudaMemcpyDeviceToHost));
+        IB_CUDA(cudaMemcpy(hres.data(), t->learned_resid, 8 * nrows, cudaMemcpyDeviceToHost));
+        for (int64_t i = 0; i < nrows; ++i) {
+            t->learned_accepted += hacc[i] != 0;
+            t->learned_checked += std::isfinite(hres[i]) ? 1 : 0;
+        }
+    }
     // pack per field
     for (int f = 0; f < fk.nf; ++f) {
         IbOp& op = t->ops[op_first + f];
@@ -1573,11 +1795,12 @@ extern "C" void ib_table_free(ib_table* t) {
     for (int i = 0; i < IB_MAX_OPS; ++i) free_op(t->ops[i]);
     for (int f = 0; f < 4; ++f)
         if (t->mask_pad[f]) cudaFree(t->mask_pad[f]);
+    if (t->learned_resid) cudaFree(t->learned_resid);
     delete t;
 }
 
 static ib_status build_impl(const ib_grid* grid, const double* sdf, ib_bc bc, ib_form form, const ib_opts* opts_in,
-                            ib_table** out, cudaStream_t s) {
+                            ib_mlp* mlp, double accept_tol, ib_table** out, cudaStream_t s) {
     double t0 = ib_wall_seconds();
     if (!grid || !sdf || !out) {
         ib_set_error("null argument");
@@ -1699,6 +1922,10 @@ static ib_status build_impl(const ib_grid* grid, const double* sdf, ib_bc bc, ib
         fk.fkind[0] = 0;
         fk.feta[0] = o.eta_p;
         fk.vector_bc = false;
+        fk.mlp = mlp;
+        fk.grid = grid;
+        fk.sdf = sdf;
+        fk.accept_tol = accept_tol;
         t->nops = 1;
         if ((st = run_fit(t, g, fk, bp_index, bp_xb, bp_n, 0, s, tmp)) != IB_OK) return fail(st);
     } else {
@@ -1763,7 +1990,41 @@ static ib_status build_impl(const ib_grid* grid, const double* sdf, ib_bc bc, ib
 extern "C" ib_status ib_build_stencils(const ib_grid* grid, const double* sdf_dev, ib_bc bc, ib_form form,
                                        const ib_opts* opts, ib_table** out, void* stream) {
     ib_set_error("");
-    return build_impl(grid, sdf_dev, bc, form, opts, out, (cudaStream_t)stream);
+    return build_impl(grid, sdf_dev, bc, form, opts, nullptr, -1.0, out, (cudaStream_t)stream);
+}
+
+extern "C" ib_status ib_build_stencils_learned(const ib_grid* grid, const double* sdf_dev, ib_bc bc,
+                                               const ib_opts* opts, ib_mlp* mlp, double accept_tol,
+                                               ib_table** out, void* stream) {
+    ib_set_error("");
+    if (!mlp) {
+        ib_set_error("null network");
+        return IB_ERR_ARG;
+    }
+    if (!grid || grid->ndim != ib_mlp_ndim(mlp) || !opts || opts->space_order != ib_mlp_order(mlp)) {
+        ib_set_error("the network was configured for another dimension or space order");
+        return IB_ERR_ARG;
+    }
+    return build_impl(grid, sdf_dev, bc, IB_SECOND_ORDER, opts, mlp, accept_tol, out, (cudaStream_t)stream);
+}
+
+extern "C" ib_status ib_table_learned(const ib_table* t, int64_t* n_checked, int64_t* n_accepted,
+                                      double* resid_host) {
+    if (!t) {
+        ib_set_error("null table");
+        return IB_ERR_ARG;
+    }
+    if (n_checked) *n_checked = t->learned_checked;
+    if (n_accepted) *n_accepted = t->learned_accepted;
+    if (resid_host && t->nops > 0) {
+        const int64_t n = t->ops[0].nrows;
+        if (t->learned_resid) {
+            IB_CUDA(cudaMemcpy(resid_host, t->learned_resid, 8 * n, cudaMemcpyDeviceToHost));
+        } else {
+            for (int64_t i = 0; i < n; ++i) resid_host[i] = NAN;
+        }
+    }
+    return IB_OK;
 }
 
 extern "C" ib_status ib_table_stats(const ib_table* t, ib_table_info* info) {

@@ -138,7 +138,22 @@ struct ib_table {
     int64_t n_bp = 0, n_fail = 0, n_grown = 0, n_reduced = 0;
     double setup_seconds = 0.0;
     int64_t table_bytes = 0;
+    // learned rows (ib_build_stencils_learned)
+    double* learned_resid = nullptr;      // [rows of op 0]
+    int64_t learned_rows = 0, learned_checked = 0, learned_accepted = 0;
 };
+
+// learned-stencil network (ib_mlp.cu)
+int ib_mlp_out_count(const ib_mlp* m);
+double ib_mlp_out_radius(const ib_mlp* m);
+int ib_mlp_ndim(const ib_mlp* m);
+int ib_mlp_order(const ib_mlp* m);
+const int32_t* ib_mlp_lut(const ib_mlp* m, int* R);
+// predictions Y[n][n_out] (FP32) for the given linear node indices
+ib_status ib_mlp_predict_nodes(ib_mlp* m, const ib_grid* grid, const double* sdf, const int64_t* nodes,
+                               int64_t n, ib_bc bc, float* Y, cudaStream_t s);
+// order-preserving compaction: indices i < n with flags[i] != 0 (device list allocated with cudaMalloc)
+ib_status ib_compact(const uint8_t* flags, int64_t n, int64_t** out, int64_t* count, cudaStream_t s);
 
 // implemented in ib_build.cu
 ib_status ib_table_bins(ib_table* t, int op, bool transposed, int tx, int ty, int tz,

@@ -21,7 +21,9 @@ SECOND_ORDER, FIRST_ORDER_STAGGERED = 0, 1
 EXPORTS = ["ib_opts_default", "ib_build_stencils", "ib_table_free", "ib_table_stats", "ib_table_export",
            "ib_forward", "ib_checkpoint_bytes", "ib_adjoint", "ib_forward_batch", "ib_sync_status",
            "ib_last_error", "ib_version", "ib_profile_enable", "ib_profile_count", "ib_profile_get",
-           "ib_forward_noalloc"]
+           "ib_forward_noalloc", "ib_mlp_create", "ib_mlp_free", "ib_mlp_info", "ib_mlp_buffers",
+           "ib_mlp_sync_weights", "ib_mlp_features", "ib_mlp_forward", "ib_mlp_train_step",
+           "ib_mlp_targets", "ib_build_stencils_learned", "ib_table_learned"]
 
 
 class IbError(RuntimeError):
@@ -49,6 +51,12 @@ class TableInfo(ctypes.Structure):
                 ("n_boundary_points", ctypes.c_int64), ("n_rank_failures", ctypes.c_int64),
                 ("n_grown", ctypes.c_int64), ("n_reduced", ctypes.c_int64),
                 ("table_bytes", ctypes.c_int64), ("setup_seconds", ctypes.c_double)]
+
+
+class MlpConfig(ctypes.Structure):
+    _fields_ = [("ndim", ctypes.c_int32), ("space_order", ctypes.c_int32),
+                ("n_hidden", ctypes.c_int32), ("n_layers", ctypes.c_int32),
+                ("in_radius", ctypes.c_double), ("out_radius", ctypes.c_double)]
 
 
 class Shot(ctypes.Structure):
@@ -104,6 +112,31 @@ def load(path=LIB_PATH):
     L.ib_profile_get.restype = i32
     L.ib_forward_noalloc.argtypes = [vp, ctypes.POINTER(Shot), dbl, i32, vp]
     L.ib_forward_noalloc.restype = i32
+    fp = ctypes.POINTER(vp)
+    L.ib_mlp_create.argtypes = [ctypes.POINTER(MlpConfig), fp]
+    L.ib_mlp_create.restype = i32
+    L.ib_mlp_free.argtypes = [vp]
+    L.ib_mlp_free.restype = None
+    L.ib_mlp_info.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), ctypes.POINTER(i64)]
+    L.ib_mlp_info.restype = i32
+    L.ib_mlp_buffers.argtypes = [vp, fp, fp, fp, fp]
+    L.ib_mlp_buffers.restype = i32
+    L.ib_mlp_sync_weights.argtypes = [vp, vp]
+    L.ib_mlp_sync_weights.restype = i32
+    L.ib_mlp_features.argtypes = [vp, ctypes.POINTER(Grid), vp, vp, i64, i32, vp, vp]
+    L.ib_mlp_features.restype = i32
+    L.ib_mlp_forward.argtypes = [vp, vp, i64, vp, vp]
+    L.ib_mlp_forward.restype = i32
+    L.ib_mlp_train_step.argtypes = [vp, vp, vp, vp, i64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                    ctypes.c_float, vp, vp]
+    L.ib_mlp_train_step.restype = i32
+    L.ib_mlp_targets.argtypes = [vp, vp, vp, vp, i64, ctypes.POINTER(i64), vp]
+    L.ib_mlp_targets.restype = i32
+    L.ib_build_stencils_learned.argtypes = [ctypes.POINTER(Grid), vp, i32, ctypes.POINTER(Opts), vp, dbl,
+                                            fp, vp]
+    L.ib_build_stencils_learned.restype = i32
+    L.ib_table_learned.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), vp]
+    L.ib_table_learned.restype = i32
     _LIB = L
     return L
 
@@ -175,6 +208,135 @@ def ib_build_stencils(sdf, h, bc="free", form="second", space_order=4, opts=None
             L.ib_table_free(handle)
         _check(st)
     return Table(handle, g.ndim, tuple(sdf.shape), float(h), fm, st)
+
+
+def _grid(sdf, h):
+    g = Grid()
+    g.ndim = sdf.dim()
+    rev = list(reversed(sdf.shape))
+    for a in range(3):
+        g.n[a] = rev[a] if a < len(rev) else 1
+    g.h = float(h)
+    return g
+
+
+def ib_build_stencils_learned(sdf, h, mlp, bc="free", space_order=4, accept_tol=1e-6, opts=None,
+                              stream=None):
+    """Second-order table whose rows take the network's prediction where it is
+    exact to ``accept_tol`` and the constrained fit elsewhere."""
+    L = load()
+    assert sdf.is_cuda and sdf.dtype == torch.float64 and sdf.is_contiguous()
+    g = _grid(sdf, h)
+    o = opts if opts is not None else ib_opts_default(space_order)
+    o.space_order = int(space_order)
+    handle = ctypes.c_void_p()
+    b = FREE if bc in ("free", FREE) else RIGID
+    st = L.ib_build_stencils_learned(ctypes.byref(g), _ptr(sdf), b, ctypes.byref(o), mlp.handle,
+                                     float(accept_tol), ctypes.byref(handle), _stream(stream))
+    if st != IB_OK:
+        if handle.value:
+            L.ib_table_free(handle)
+        _check(st)
+    return Table(handle, g.ndim, tuple(sdf.shape), float(h), SECOND_ORDER, st)
+
+
+def ib_table_learned(table):
+    """(rows checked, rows accepted, per-row residual as numpy)."""
+    nr = ib_table_stats(table)["rows"][0] if ib_table_stats(table)["n_ops"] else 0
+    res = np.full(max(nr, 1), np.nan)
+    c, a = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().ib_table_learned(table.handle, ctypes.byref(c), ctypes.byref(a),
+                                   res.ctypes.data_as(ctypes.c_void_p)))
+    return c.value, a.value, res[:nr]
+
+
+class Mlp:
+    """Owner of an ``ib_mlp*`` (learned stencil network on the current device)."""
+
+    def __init__(self, ndim, space_order, n_hidden=256, n_layers=4, in_radius=4.0, out_radius=None):
+        L = load()
+        cfg = MlpConfig()
+        cfg.ndim = int(ndim)
+        cfg.space_order = int(space_order)
+        cfg.n_hidden = int(n_hidden)
+        cfg.n_layers = int(n_layers)
+        cfg.in_radius = float(in_radius)
+        cfg.out_radius = float(out_radius if out_radius is not None else (min(space_order, 4) + 1) / 2.0)
+        self.cfg = cfg
+        h = ctypes.c_void_p()
+        _check(L.ib_mlp_create(ctypes.byref(cfg), ctypes.byref(h)))
+        self.handle = h
+        n_in, n_out, n_par = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+        _check(L.ib_mlp_info(h, ctypes.byref(n_in), ctypes.byref(n_out), ctypes.byref(n_par)))
+        self.n_in, self.n_out, self.n_params = n_in.value, n_out.value, n_par.value
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _LIB is not None:
+            _LIB.ib_mlp_free(self.handle)
+            self.handle = None
+
+    def buffers(self):
+        """Library-owned device buffers as torch views: params, grads, adam_m, adam_v."""
+        ptrs = [ctypes.c_void_p() for _ in range(4)]
+        _check(load().ib_mlp_buffers(self.handle, *[ctypes.byref(p) for p in ptrs]))
+        out = []
+        for p in ptrs:
+            out.append(_device_view(p.value, self.n_params))
+        return out
+
+    def set_params(self, values, stream=None):
+        params = self.buffers()[0]
+        params.copy_(torch.as_tensor(values, dtype=torch.float32, device=params.device))
+        _check(load().ib_mlp_sync_weights(self.handle, _stream(stream)))
+
+
+def _device_view(ptr, n):
+    """torch float32 view of n library-owned device floats (no copy)."""
+    class _Arr:
+        pass
+    a = _Arr()
+    a.__cuda_array_interface__ = {"shape": (int(n),), "typestr": "<f4", "data": (int(ptr), False),
+                                  "version": 3, "strides": None}
+    return torch.as_tensor(a, device="cuda")
+
+
+def ib_mlp_features(mlp, sdf, h, nodes, bc="free", stream=None):
+    """bfloat16 features [n][n_in] of the nodes (int64 linear indices)."""
+    assert nodes.dtype == torch.int64 and nodes.is_cuda
+    X = torch.empty((nodes.numel(), mlp.n_in), dtype=torch.bfloat16, device=sdf.device)
+    b = FREE if bc in ("free", FREE) else RIGID
+    _check(load().ib_mlp_features(mlp.handle, ctypes.byref(_grid(sdf, h)), _ptr(sdf), _ptr(nodes),
+                                  int(nodes.numel()), b, _ptr(X), _stream(stream)))
+    return X
+
+
+def ib_mlp_forward(mlp, X, stream=None):
+    assert X.dtype == torch.bfloat16 and X.is_contiguous() and X.shape[1] == mlp.n_in
+    Y = torch.empty((X.shape[0], mlp.n_out), dtype=torch.float32, device=X.device)
+    _check(load().ib_mlp_forward(mlp.handle, _ptr(X), int(X.shape[0]), _ptr(Y), _stream(stream)))
+    return Y
+
+
+def ib_mlp_train_step(mlp, X, T, idx, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, loss=None, stream=None):
+    """One Adam step on rows idx of (X, T); returns the device loss tensor."""
+    assert X.dtype == torch.bfloat16 and T.dtype == torch.float32 and idx.dtype == torch.int64
+    if loss is None:
+        loss = torch.empty(1, dtype=torch.float32, device=X.device)
+    _check(load().ib_mlp_train_step(mlp.handle, _ptr(X), _ptr(T), _ptr(idx), int(idx.numel()), float(lr),
+                                    float(beta1), float(beta2), float(eps), _ptr(loss), _stream(stream)))
+    return loss
+
+
+def ib_mlp_targets(table, mlp, stream=None):
+    """(nodes int64 [n], targets float32 [n][n_out]) of the table's trainable rows."""
+    nr = ib_table_stats(table)["rows"][0]
+    dev = torch.device("cuda", torch.cuda.current_device())
+    nodes = torch.empty(max(nr, 1), dtype=torch.int64, device=dev)
+    T = torch.empty((max(nr, 1), mlp.n_out), dtype=torch.float32, device=dev)
+    n = ctypes.c_int64()
+    _check(load().ib_mlp_targets(table.handle, mlp.handle, _ptr(nodes), _ptr(T), int(nr), ctypes.byref(n),
+                                 _stream(stream)))
+    return nodes[:n.value], T[:n.value]
 
 
 def ib_table_stats(table):
