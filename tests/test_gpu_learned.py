@@ -220,7 +220,12 @@ def test_single_row_exact_prediction_is_accepted(ib, hills):
     net = ib.Mlp(3, 8, n_hidden=8, n_layers=1)
     plain = ib.ib_build_stencils(sdf, H, "free", "second", 8)
     nodes, T = ib.ib_mlp_targets(plain, net)
-    k = int(len(nodes) // 2)
+    # a row whose BC rows leave basis polynomials free (the check has content)
+    probe = ib.ib_build_stencils_learned(sdf, H, net, bc="free", space_order=8, accept_tol=-1.0)
+    _, _, res0 = ib.ib_table_learned(probe)
+    node_row = {int(n): r for r, n in enumerate(probe.export(0)["row_node"])}
+    ok = [k for k in range(len(nodes)) if np.isfinite(res0[node_row[int(nodes[k])]])]
+    k = ok[len(ok) // 2]
     p = np.zeros(net.n_params, np.float32)
     p[-net.n_out:] = T[k].cpu().numpy()
     net.set_params(p)
