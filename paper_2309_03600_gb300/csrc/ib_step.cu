@@ -534,6 +534,16 @@ struct StagArgs {
     int rec_step;
 };
 
+// asynchronous global -> shared copy of B bytes (zero fill when !valid)
+template <int B>
+__device__ __forceinline__ void cp_async(void* dst, const void* src, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(smem_u32(dst)), "l"(src), "n"(B),
+                 "r"(valid ? B : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // consumer side: correction of row i of this tile's list = sum of its partials
 template <typename T>
 __device__ __forceinline__ T plan_row_sum(const StagPlan<T>& P, int32_t i) {
@@ -542,31 +552,48 @@ __device__ __forceinline__ T plan_row_sum(const StagPlan<T>& P, int32_t i) {
     return c;
 }
 
+// producer side, first part: stage up to STG of this tile's entries in shared memory
+template <typename T, int STG>
+__device__ __forceinline__ int32_t plan_stage(const StagPlan<T>& P, int64_t tile, int32_t* smeta, T* sw, int tid) {
+    const int32_t e0 = P.eptr[tile], e1 = P.eptr[tile + 1];
+    const int32_t n = e1 - e0 < STG ? e1 - e0 : STG;
+    for (int32_t i = tid; i < n; i += 256) {
+        cp_async<4>(&smeta[i], P.emeta + e0 + i, true);
+        cp_async<(int)sizeof(T)>(&sw[i], P.ew + e0 + i, true);
+    }
+    return n;
+}
+
 // producer side: partial[pid] = sum of w * fnew[field][slot] over the pid's entries in this tile.
 // A tile's entries are ordered by their rank within the pid, then by pid, so
-// the lanes of a warp add into different partial sums.
+// the lanes of a warp add into different partial sums.  The first `nst`
+// entries were staged in shared memory while the tile loaded.
 template <typename T, int SLOTS>
-__device__ __forceinline__ void plan_produce(const StagPlan<T>& P, int64_t tile, const T* fnew, T* psum, int tid) {
+__device__ __forceinline__ void plan_produce(const StagPlan<T>& P, int64_t tile, const T* fnew, T* psum,
+                                             const int32_t* smeta, const T* sw, int32_t nst, int tid) {
     const int32_t q0 = P.qptr[tile], nq = P.qptr[tile + 1] - q0;
     const int32_t e0 = P.eptr[tile], e1 = P.eptr[tile + 1];
     for (int32_t k = tid; k < nq; k += 256) psum[k] = (T)0;
     __syncthreads();
+    for (int32_t i = tid; i < nst; i += 256) {
+        const uint32_t mm = (uint32_t)smeta[i];
+        atomicAdd(&psum[(mm >> 11) & 0xfffff], sw[i] * fnew[(mm >> 31) * SLOTS + (mm & 0x7ff)]);
+    }
     constexpr int U = 8;
-    for (int32_t base = e0 + tid; base < e1; base += 256 * U) {
+    for (int32_t base = e0 + nst + tid; base < e1; base += 256 * U) {
         int32_t m[U];
         T w[U];
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             const int32_t e = base + u * 256;
-            m[u] = e < e1 ? P.emeta[e] : -1;
+            m[u] = e < e1 ? P.emeta[e] : 0;
             w[u] = e < e1 ? P.ew[e] : (T)0;
         }
 #pragma unroll
         for (int u = 0; u < U; ++u) {
             if (base + u * 256 >= e1) continue;
             const uint32_t mm = (uint32_t)m[u];
-            const T f = fnew[(mm >> 31) * SLOTS + (mm & 0x7ff)];
-            atomicAdd(&psum[(mm >> 11) & 0xfffff], w[u] * f);
+            atomicAdd(&psum[(mm >> 11) & 0xfffff], w[u] * fnew[(mm >> 31) * SLOTS + (mm & 0x7ff)]);
         }
     }
     __syncthreads();
@@ -574,24 +601,39 @@ __device__ __forceinline__ void plan_produce(const StagPlan<T>& P, int64_t tile,
 }
 
 // v^{n+1/2} = v^{n-1/2} + (dt / rho) G_mod p^n on a 64 x TZ tile (256 threads as 64 x 4,
-// TZ / 4 points per thread)
-template <typename T, int H, int TX, int TZ, int MAXQ>
+// TZ / 4 points per thread); the p tile and the producer entries arrive by cp.async
+template <typename T, int H, int TX, int TZ, int MAXQ, int STG>
 __global__ void __launch_bounds__(256, 4) k_stag_v2d(StagArgs<T> a) {
     static_assert(TX == 64 && TZ % 4 == 0, "64-wide tiles, 4 thread rows");
     constexpr int NP = TZ / 4, SL = TZ * TX;
-    __shared__ T tile[TZ + 2 * H][TX + 2 * H];
+    __shared__ __align__(16) T tile[TZ + 2 * H][TX + 2 * H];
     __shared__ T acc[2 * SL];                        // a_x, a_z; then the new v_x, v_z
     __shared__ T psum[MAXQ];
+    __shared__ int32_t smeta[STG];
+    __shared__ T sw[STG];
     const int tid = threadIdx.x, tx = tid & 63, ty = tid >> 6;
     const int64_t blk = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
-    const int sb = a.step_base ? *a.step_base : 0;
-    record_receivers(a.rec, a.p, a.traces, a.nt, a.rec_step < 0 && sb == 0 ? -1 : sb + a.rec_step, blk * 256 + tid);
     const int64_t x0 = (int64_t)blockIdx.x * TX, z0 = (int64_t)blockIdx.y * TZ;
     const Layout& L = a.L;
     const int64_t origin = L.base + z0 * L.px + x0;
+    {
+        const T* pb = a.p + origin - H * L.px - H;
+#pragma unroll
+        for (int lz = ty; lz < TZ + 2 * H; lz += 4) {
+            const bool zok = z0 + lz - H < L.nz + H;
+            const T* row = pb + lz * L.px;
+            for (int lx = tx; lx < TX + 2 * H; lx += 64) {
+                const bool ok = zok && x0 + lx - H < L.nx + H;
+                cp_async<(int)sizeof(T)>(&tile[lz][lx], ok ? row + lx : a.p, ok);
+            }
+        }
+    }
+    const int32_t nst = plan_stage<T, STG>(a.pv, blk, smeta, sw, tid);
+    cp_async_commit();
+    const int sb = a.step_base ? *a.step_base : 0;
+    record_receivers(a.rec, a.p, a.traces, a.nt, sb + a.rec_step, blk * 256 + tid);
     const int32_t r0 = a.pv.rptr[blk], r1 = a.pv.rptr[blk + 1];
-    // the update's own operands and this tile's row corrections first: their
-    // latency overlaps the tile load
+    // the update's own operands and this tile's row corrections while the copies fly
     T vx[NP], vz[NP], bx[NP], bz[NP];
 #pragma unroll
     for (int k = 0; k < NP; ++k) {
@@ -603,20 +645,13 @@ __global__ void __launch_bounds__(256, 4) k_stag_v2d(StagArgs<T> a) {
         bx[k] = in ? a.bx[q] : (T)0;
         bz[k] = in ? a.bz[q] : (T)0;
     }
-    const T* pb = a.p + origin - H * L.px - H;
-#pragma unroll
-    for (int lz = ty; lz < TZ + 2 * H; lz += 4) {
-        const bool zok = z0 + lz - H < L.nz + H;
-        const T* row = pb + lz * L.px;
-        for (int lx = tx; lx < TX + 2 * H; lx += 64)
-            tile[lz][lx] = (zok && x0 + lx - H < L.nx + H) ? row[lx] : (T)0;
-    }
     T corr = 0;
     int32_t cslot = 0;
     if (r0 + tid < r1) {
         corr = plan_row_sum(a.pv, r0 + tid);
         cslot = a.pv.rslot[r0 + tid];
     }
+    cp_async_wait_all();
     __syncthreads();
     T ax[NP], az[NP];
 #pragma unroll
@@ -668,23 +703,46 @@ __global__ void __launch_bounds__(256, 4) k_stag_v2d(StagArgs<T> a) {
         a.vx[q] = nvx;
         a.vz[q] = nvz;
     }
-    if (produce) plan_produce<T, SL>(a.pv, blk, acc, psum, tid);
+    if (produce) plan_produce<T, SL>(a.pv, blk, acc, psum, smeta, sw, nst, tid);
 }
 
 // p^{n+1} = p^n + dt rho c^2 D_mod v^{n+1/2} (+ source) on a 64 x TZ tile
-template <typename T, int H, int TX, int TZ, int MAXQ>
+template <typename T, int H, int TX, int TZ, int MAXQ, int STG>
 __global__ void __launch_bounds__(256, 4) k_stag_p2d(StagArgs<T> a) {
     static_assert(TX == 64 && TZ % 4 == 0, "64-wide tiles, 4 thread rows");
     constexpr int NP = TZ / 4, SL = TZ * TX;
-    __shared__ T tvx[TZ][TX + 2 * H];
-    __shared__ T tvz[TZ + 2 * H][TX];
+    __shared__ __align__(16) T tvx[TZ][TX + 2 * H];
+    __shared__ __align__(16) T tvz[TZ + 2 * H][TX];
     __shared__ T acc[SL];
     __shared__ T psum[MAXQ];
+    __shared__ int32_t smeta[STG];
+    __shared__ T sw[STG];
     const int tid = threadIdx.x, tx = tid & 63, ty = tid >> 6;
     const int64_t blk = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
     const int64_t x0 = (int64_t)blockIdx.x * TX, z0 = (int64_t)blockIdx.y * TZ;
     const Layout& L = a.L;
     const int64_t origin = L.base + z0 * L.px + x0;
+    {
+        const T* vb = a.vx + origin - H;
+#pragma unroll
+        for (int lz = ty; lz < TZ; lz += 4) {
+            const bool zok = z0 + lz < L.nz + H;
+            const T* row = vb + lz * L.px;
+            for (int lx = tx; lx < TX + 2 * H; lx += 64) {
+                const bool ok = zok && x0 + lx - H < L.nx + H;
+                cp_async<(int)sizeof(T)>(&tvx[lz][lx], ok ? row + lx : a.vx, ok);
+            }
+        }
+        const T* wb = a.vz + origin - H * L.px;
+        const bool xok = x0 + tx < L.nx + H;
+#pragma unroll
+        for (int lz = ty; lz < TZ + 2 * H; lz += 4) {
+            const bool ok = xok && z0 + lz - H < L.nz + H;
+            cp_async<(int)sizeof(T)>(&tvz[lz][tx], ok ? wb + lz * L.px + tx : a.vz, ok);
+        }
+    }
+    const int32_t nst = plan_stage<T, STG>(a.pp, blk, smeta, sw, tid);
+    cp_async_commit();
     const int32_t r0 = a.pp.rptr[blk], r1 = a.pp.rptr[blk + 1];
     T pv[NP], kv[NP];
 #pragma unroll
@@ -695,21 +753,6 @@ __global__ void __launch_bounds__(256, 4) k_stag_p2d(StagArgs<T> a) {
         pv[k] = in ? a.p[q] : (T)0;
         kv[k] = in ? a.kp[q] : (T)0;
     }
-    {
-        const T* vb = a.vx + origin - H;
-#pragma unroll
-        for (int lz = ty; lz < TZ; lz += 4) {
-            const bool zok = z0 + lz < L.nz + H;
-            const T* row = vb + lz * L.px;
-            for (int lx = tx; lx < TX + 2 * H; lx += 64)
-                tvx[lz][lx] = (zok && x0 + lx - H < L.nx + H) ? row[lx] : (T)0;
-        }
-        const T* wb = a.vz + origin - H * L.px;
-        const bool xok = x0 + tx < L.nx + H;
-#pragma unroll
-        for (int lz = ty; lz < TZ + 2 * H; lz += 4)
-            tvz[lz][tx] = (xok && z0 + lz - H < L.nz + H) ? wb[lz * L.px + tx] : (T)0;
-    }
     T corr = 0;
     int32_t cslot = 0;
     if (r0 + tid < r1) {
@@ -719,6 +762,7 @@ __global__ void __launch_bounds__(256, 4) k_stag_p2d(StagArgs<T> a) {
     const bool has_src = a.src.n > 0 && a.src_tile[blk] != 0;
     if (has_src || r1 > r0)
         for (int i = tid; i < SL; i += 256) acc[i] = (T)0;
+    cp_async_wait_all();
     __syncthreads();
     T s[NP];
 #pragma unroll
@@ -757,7 +801,7 @@ __global__ void __launch_bounds__(256, 4) k_stag_p2d(StagArgs<T> a) {
         if (x0 + tx >= L.nx || z0 + lz >= L.nz) continue;
         a.p[origin + lz * L.px + tx] = s[k];
     }
-    if (produce) plan_produce<T, SL>(a.pp, blk, acc, psum, tid);
+    if (produce) plan_produce<T, SL>(a.pp, blk, acc, psum, smeta, sw, nst, tid);
 }
 
 // ---------------------------------------------------------------------------
@@ -1223,8 +1267,8 @@ static ib_status forward_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, 
 // STAG_MAXQ partial sums produced per tile.
 static const int STAG_TX = 64, STAG_MAXQ = 1024;
 static_assert(STAG_TX * 32 <= 2048 && STAG_MAXQ <= (1 << 20), "packed producer entries: 11-bit slot, 20-bit position");
-template <typename T> struct StagTile { static const int TZ = 32; };
-template <> struct StagTile<double> { static const int TZ = 16; };
+template <typename T> struct StagTile { static const int TZ = 16, STG = 2048; };
+template <> struct StagTile<double> { static const int TZ = 16, STG = 512; };
 
 struct PlanOp {
     int op;       // consumer operator
@@ -1280,82 +1324,76 @@ static ib_status build_stag_plan(ib_table* t, const std::vector<PlanOp>& ops, in
             }
         }
     }
-    // partial ids: one per (row, producer tile), numbered row by row
-    std::stable_sort(ent.begin(), ent.end(), [](const Ent& a, const Ent& b) {
-        return a.row != b.row ? a.row < b.row : a.ptile < b.ptile;
-    });
+    // partial ids: one per (row, producer tile), numbered row by row (entries
+    // arrive grouped by row; order each row's entries by producer tile)
     const int64_t nrow = (int64_t)rows.size(), nent = (int64_t)ent.size();
-    std::vector<int32_t> pid(nent), rpb(nrow, 0), rpe(nrow, 0);
+    for (int64_t i = 0; i < nent;) {
+        int64_t j = i;
+        while (j < nent && ent[j].row == ent[i].row) ++j;
+        std::stable_sort(ent.begin() + i, ent.begin() + j, [](const Ent& x, const Ent& y) { return x.ptile < y.ptile; });
+        i = j;
+    }
+    std::vector<int32_t> pid(nent), rank(nent), rpb(nrow, 0), rpe(nrow, 0);
     int32_t npid = 0;
     for (int64_t i = 0; i < nent; ++i) {
-        if (i == 0 || ent[i].row != ent[i - 1].row || ent[i].ptile != ent[i - 1].ptile) {
-            if (i == 0 || ent[i].row != ent[i - 1].row) rpb[ent[i].row] = npid;
+        const bool new_row = i == 0 || ent[i].row != ent[i - 1].row;
+        if (new_row || ent[i].ptile != ent[i - 1].ptile) {
+            if (new_row) rpb[ent[i].row] = npid;
             ++npid;
+            rank[i] = 0;
+        } else {
+            rank[i] = rank[i - 1] + 1;
         }
         pid[i] = npid - 1;
         rpe[ent[i].row] = npid;
     }
-    // producer side: entries grouped by tile, then pid
-    std::vector<int64_t> order(nent);
-    for (int64_t i = 0; i < nent; ++i) order[i] = i;
-    // rank of each entry within its pid (entries of a pid are adjacent after the sort above)
-    std::vector<int32_t> rank(nent, 0);
-    for (int64_t i = 1; i < nent; ++i) rank[i] = pid[i] == pid[i - 1] ? rank[i - 1] + 1 : 0;
-    std::stable_sort(order.begin(), order.end(), [&](int64_t a, int64_t b) {
-        return ent[a].ptile != ent[b].ptile ? ent[a].ptile < ent[b].ptile : pid[a] < pid[b];
-    });
+    // producer side: entries grouped by tile (counting sort keeps the pid order)
     std::vector<int32_t> eptr(ntiles + 1, 0), qptr(ntiles + 1, 0), emeta(nent), qpid;
     std::vector<T> ew(nent);
-    int max_q = 0;
+    std::vector<int64_t> order(nent);
+    for (int64_t i = 0; i < nent; ++i) eptr[ent[i].ptile + 1]++;
+    for (int64_t tl = 0; tl < ntiles; ++tl) eptr[tl + 1] += eptr[tl];
     {
-        int64_t i = 0;
-        for (int64_t tl = 0; tl < ntiles; ++tl) {
-            eptr[tl] = (int32_t)i;
-            qptr[tl] = (int32_t)qpid.size();
-            const int32_t q0 = (int32_t)qpid.size();
-            const int64_t i0 = i;
-            for (; i < nent && ent[order[i]].ptile == tl; ++i)
-                if ((int32_t)qpid.size() == q0 || qpid.back() != pid[order[i]]) qpid.push_back(pid[order[i]]);
-            max_q = std::max(max_q, (int)qpid.size() - q0);
-            // within the tile: by rank, then pid (adjacent lanes hit different partial sums)
-            std::stable_sort(order.begin() + i0, order.begin() + i, [&](int64_t a, int64_t b) {
-                return rank[a] != rank[b] ? rank[a] < rank[b] : pid[a] < pid[b];
-            });
-            std::map<int32_t, int32_t> pos;
-            for (int64_t k = i0; k < i; ++k) pos[pid[order[k]]] = 0;
-            {
-                int32_t c = 0;
-                for (auto& kv : pos) kv.second = c++;
-            }
-            for (int64_t k = i0; k < i; ++k) {
-                const Ent& e = ent[order[k]];
-                emeta[k] = (int32_t)((uint32_t)e.field << 31 | (uint32_t)pos[pid[order[k]]] << 11 | (uint32_t)e.slot);
-                ew[k] = (T)e.w;
-            }
-        }
-        eptr[ntiles] = (int32_t)i;
-        qptr[ntiles] = (int32_t)qpid.size();
+        std::vector<int32_t> fill(eptr.begin(), eptr.end() - 1);
+        for (int64_t i = 0; i < nent; ++i) order[fill[ent[i].ptile]++] = i;
     }
+    int max_q = 0;
+    for (int64_t tl = 0; tl < ntiles; ++tl) {
+        const int64_t i0 = eptr[tl], i1 = eptr[tl + 1];
+        qptr[tl] = (int32_t)qpid.size();
+        const int64_t q0 = (int64_t)qpid.size();
+        for (int64_t i = i0; i < i1; ++i)
+            if ((int64_t)qpid.size() == q0 || qpid.back() != pid[order[i]]) qpid.push_back(pid[order[i]]);
+        max_q = std::max(max_q, (int)((int64_t)qpid.size() - q0));
+        // within the tile: by rank, then pid (adjacent lanes add into different partial sums)
+        std::sort(order.begin() + i0, order.begin() + i1, [&](int64_t x, int64_t y) {
+            return rank[x] != rank[y] ? rank[x] < rank[y] : pid[x] < pid[y];
+        });
+        for (int64_t k = i0; k < i1; ++k) {
+            const Ent& e = ent[order[k]];
+            const int32_t pos = (int32_t)(std::lower_bound(qpid.begin() + q0, qpid.end(), pid[order[k]]) -
+                                          (qpid.begin() + q0));
+            emeta[k] = (int32_t)((uint32_t)e.field << 31 | (uint32_t)pos << 11 | (uint32_t)e.slot);
+            ew[k] = (T)e.w;
+        }
+    }
+    qptr[ntiles] = (int32_t)qpid.size();
     if (max_q > STAG_MAXQ) {
         ib_set_error("a staggered step tile holds more correction partial sums than the kernel's buffer");
         return IB_ERR_STATE;
     }
-    // consumer side: rows grouped by tile
-    std::vector<int64_t> rorder(nrow);
-    for (int64_t i = 0; i < nrow; ++i) rorder[i] = i;
-    std::stable_sort(rorder.begin(), rorder.end(), [&](int64_t a, int64_t b) { return rows[a].ctile < rows[b].ctile; });
+    // consumer side: rows grouped by tile (counting sort)
     std::vector<int32_t> rptr(ntiles + 1, 0), rslot(nrow), rb(nrow), re(nrow);
+    for (int64_t r = 0; r < nrow; ++r) rptr[rows[r].ctile + 1]++;
+    for (int64_t tl = 0; tl < ntiles; ++tl) rptr[tl + 1] += rptr[tl];
     {
-        int64_t i = 0;
-        for (int64_t tl = 0; tl < ntiles; ++tl) {
-            rptr[tl] = (int32_t)i;
-            for (; i < nrow && rows[rorder[i]].ctile == tl; ++i) {
-                rslot[i] = rows[rorder[i]].cslot;
-                rb[i] = rpb[rorder[i]];
-                re[i] = rpe[rorder[i]];
-            }
+        std::vector<int32_t> fill(rptr.begin(), rptr.end() - 1);
+        for (int64_t r = 0; r < nrow; ++r) {
+            const int32_t i = fill[rows[r].ctile]++;
+            rslot[i] = rows[r].cslot;
+            rb[i] = rpb[r];
+            re[i] = rpe[r];
         }
-        rptr[ntiles] = (int32_t)i;
     }
     auto up = [&](auto** dst, const auto& v) -> ib_status {
         using E = typename std::decay<decltype(v[0])>::type;
@@ -1438,7 +1476,7 @@ static ib_status forward_stag(ib_table* t, const ib_shot* sh, double dt, int nt,
     a.bx = bx;
     a.bz = bz;
     a.kp = kp;
-    constexpr int TZ = StagTile<T>::TZ;
+    constexpr int TZ = StagTile<T>::TZ, STG = StagTile<T>::STG;
     // p rows read partials of v (formed by the v kernel); v rows read partials of p
     TRY(build_stag_plan<T>(t, {{2, 0, 0}, {3, 0, 1}}, TZ, S, a.pp, a.pv, s));
     TRY(build_stag_plan<T>(t, {{0, 0, 0}, {1, 1, 0}}, TZ, S, a.pv, a.pp, s));
@@ -1465,16 +1503,16 @@ static ib_status forward_stag(ib_table* t, const ib_shot* sh, double dt, int nt,
     dim3 grid2((unsigned)ntx, (unsigned)ntz);
     auto launch_step = [&](cudaStream_t st, bool prof) -> ib_status {
         auto v = [&]() {
-            if (H == 1) k_stag_v2d<T, 1, STAG_TX, TZ, STAG_MAXQ><<<grid2, 256, 0, st>>>(a);
-            else if (H == 2) k_stag_v2d<T, 2, STAG_TX, TZ, STAG_MAXQ><<<grid2, 256, 0, st>>>(a);
-            else if (H == 3) k_stag_v2d<T, 3, STAG_TX, TZ, STAG_MAXQ><<<grid2, 256, 0, st>>>(a);
-            else k_stag_v2d<T, 4, STAG_TX, TZ, STAG_MAXQ><<<grid2, 256, 0, st>>>(a);
+            if (H == 1) k_stag_v2d<T, 1, STAG_TX, TZ, STAG_MAXQ, STG><<<grid2, 256, 0, st>>>(a);
+            else if (H == 2) k_stag_v2d<T, 2, STAG_TX, TZ, STAG_MAXQ, STG><<<grid2, 256, 0, st>>>(a);
+            else if (H == 3) k_stag_v2d<T, 3, STAG_TX, TZ, STAG_MAXQ, STG><<<grid2, 256, 0, st>>>(a);
+            else k_stag_v2d<T, 4, STAG_TX, TZ, STAG_MAXQ, STG><<<grid2, 256, 0, st>>>(a);
         };
         auto pk = [&]() {
-            if (H == 1) k_stag_p2d<T, 1, STAG_TX, TZ, STAG_MAXQ><<<grid2, 256, 0, st>>>(a);
-            else if (H == 2) k_stag_p2d<T, 2, STAG_TX, TZ, STAG_MAXQ><<<grid2, 256, 0, st>>>(a);
-            else if (H == 3) k_stag_p2d<T, 3, STAG_TX, TZ, STAG_MAXQ><<<grid2, 256, 0, st>>>(a);
-            else k_stag_p2d<T, 4, STAG_TX, TZ, STAG_MAXQ><<<grid2, 256, 0, st>>>(a);
+            if (H == 1) k_stag_p2d<T, 1, STAG_TX, TZ, STAG_MAXQ, STG><<<grid2, 256, 0, st>>>(a);
+            else if (H == 2) k_stag_p2d<T, 2, STAG_TX, TZ, STAG_MAXQ, STG><<<grid2, 256, 0, st>>>(a);
+            else if (H == 3) k_stag_p2d<T, 3, STAG_TX, TZ, STAG_MAXQ, STG><<<grid2, 256, 0, st>>>(a);
+            else k_stag_p2d<T, 4, STAG_TX, TZ, STAG_MAXQ, STG><<<grid2, 256, 0, st>>>(a);
         };
         if (prof) {
             PROF_LAUNCH(kname<T>("stag_v2d_f32", "stag_v2d_f64"), st, { v(); });
