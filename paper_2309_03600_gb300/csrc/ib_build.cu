@@ -719,45 +719,70 @@ __device__ double warp_norm(const double* x, int n) {
 }
 
 // sigma_min / sigma_max of R by power / inverse iteration in one warp (large n)
-__device__ double warp_cond_ratio(const double* R, const double* invd, int n, double* x, double* y) {
-    int lane = threadIdx.x & 31;
-    for (int i = lane; i < n; i += 32) x[i] = 1.0 / sqrt((double)n);
+// sigma_min / sigma_max of R by power and inverse iteration in one warp, in
+// FP32 (the rank decision needs a few digits; GB300's FP64 pipe is the
+// constructor's bottleneck).  x, y: scratch of n floats each.
+__device__ float warp_norm_f(const float* x, int n) {
+    float s = 0.f;
+    for (int i = threadIdx.x & 31; i < n; i += 32) s += x[i] * x[i];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    return sqrtf(s);
+}
+__device__ double warp_cond_ratio(const double* R, const double* invd, int n, double* xd, double* yd) {
+    const int lane = threadIdx.x & 31;
+    float* x = (float*)xd;
+    float* y = (float*)yd;
+    for (int i = lane; i < n; i += 32) x[i] = rsqrtf((float)n);
     __syncwarp();
-    double smax2 = 0.0;
+    float smax2 = 0.f;
     for (int it = 0; it < 24; ++it) {
         for (int i = lane; i < n; i += 32) {
-            double s = 0.0;
-            for (int j = i; j < n; ++j) s += R[i * n + j] * x[j];
+            float s = 0.f;
+            for (int j = i; j < n; ++j) s += (float)R[i * n + j] * x[j];
             y[i] = s;
         }
         __syncwarp();
         for (int j = lane; j < n; j += 32) {
-            double s = 0.0;
-            for (int i = 0; i <= j; ++i) s += R[i * n + j] * y[i];
+            float s = 0.f;
+            for (int i = 0; i <= j; ++i) s += (float)R[i * n + j] * y[i];
             x[j] = s;
         }
         __syncwarp();
-        double nr = warp_norm(x, n);
+        const float nr = warp_norm_f(x, n);
+        if (!(nr > 0.f) || !(nr < 3e38f)) return 0.0;
         smax2 = nr;
         for (int i = lane; i < n; i += 32) x[i] /= nr;
         __syncwarp();
     }
-    for (int i = lane; i < n; i += 32) x[i] = 1.0 / sqrt((double)n) * (1.0 + 0.01 * (i % 7));
+    for (int i = lane; i < n; i += 32) x[i] = rsqrtf((float)n) * (1.f + 0.01f * (float)(i % 7));
     __syncwarp();
-    double nx0 = warp_norm(x, n);
+    const float nx0 = warp_norm_f(x, n);
     for (int i = lane; i < n; i += 32) x[i] /= nx0;
     __syncwarp();
-    double smin2 = 0.0;
+    float smin2 = 0.f;
     for (int it = 0; it < 40; ++it) {
-        warp_solve_RT(R, invd, n, x);
-        warp_solve_R(R, invd, n, x);
-        double nr = warp_norm(x, n);
-        if (!(nr < 1e300) || nr == 0.0) return 0.0;
-        smin2 = 1.0 / nr;
+        // R^T w = x, then R x' = w (forward and back substitution, one warp)
+        for (int k = 0; k < n; ++k) {
+            const float wk = x[k] * (float)invd[k];
+            __syncwarp();
+            if (lane == 0) x[k] = wk;
+            for (int i = k + 1 + lane; i < n; i += 32) x[i] -= (float)R[k * n + i] * wk;
+            __syncwarp();
+        }
+        for (int k = n - 1; k >= 0; --k) {
+            const float yk = x[k] * (float)invd[k];
+            __syncwarp();
+            if (lane == 0) x[k] = yk;
+            for (int i = lane; i < k; i += 32) x[i] -= (float)R[i * n + k] * yk;
+            __syncwarp();
+        }
+        const float nr = warp_norm_f(x, n);
+        if (!(nr < 3e38f) || nr == 0.f) return 0.0;
+        smin2 = 1.f / nr;
         for (int i = lane; i < n; i += 32) x[i] /= nr;
         __syncwarp();
     }
-    return sqrt(smin2 / smax2);
+    return sqrt((double)smin2 / (double)smax2);
 }
 
 // X = R^{-1} (upper triangular): thread j back-substitutes column j

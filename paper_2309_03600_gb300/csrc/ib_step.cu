@@ -1292,6 +1292,15 @@ static ib_status build_stag_plan(ib_table* t, const std::vector<PlanOp>& ops, in
     };
     std::vector<Ent> ent;
     std::vector<Row> rows;
+    {
+        int64_t nnz = 0, nr = 0;
+        for (const PlanOp& po : ops) {
+            nnz += t->ops[po.op].nnz;
+            nr += t->ops[po.op].nrows;
+        }
+        ent.reserve(nnz);
+        rows.reserve(nr);
+    }
     for (const PlanOp& po : ops) {
         const IbOp& op = t->ops[po.op];
         const int64_t nr = op.nrows, nz = op.nnz;
@@ -1324,14 +1333,28 @@ static ib_status build_stag_plan(ib_table* t, const std::vector<PlanOp>& ops, in
             }
         }
     }
-    // partial ids: one per (row, producer tile), numbered row by row (entries
-    // arrive grouped by row; order each row's entries by producer tile)
+    // partial ids: one per (row, producer tile), numbered row by row.  Entries
+    // arrive grouped by row; regroup each row's entries by producer tile (a row
+    // spans a few tiles), keeping their order within a tile.
     const int64_t nrow = (int64_t)rows.size(), nent = (int64_t)ent.size();
-    for (int64_t i = 0; i < nent;) {
-        int64_t j = i;
-        while (j < nent && ent[j].row == ent[i].row) ++j;
-        std::stable_sort(ent.begin() + i, ent.begin() + j, [](const Ent& x, const Ent& y) { return x.ptile < y.ptile; });
-        i = j;
+    {
+        std::vector<Ent> tmp;
+        std::vector<int32_t> tiles;
+        for (int64_t i = 0; i < nent;) {
+            int64_t j = i;
+            tiles.clear();
+            for (; j < nent && ent[j].row == ent[i].row; ++j)
+                if (std::find(tiles.begin(), tiles.end(), ent[j].ptile) == tiles.end()) tiles.push_back(ent[j].ptile);
+            if (tiles.size() > 1) {
+                std::sort(tiles.begin(), tiles.end());
+                tmp.clear();
+                for (int32_t tl : tiles)
+                    for (int64_t k = i; k < j; ++k)
+                        if (ent[k].ptile == tl) tmp.push_back(ent[k]);
+                std::copy(tmp.begin(), tmp.end(), ent.begin() + i);
+            }
+            i = j;
+        }
     }
     std::vector<int32_t> pid(nent), rank(nent), rpb(nrow, 0), rpe(nrow, 0);
     int32_t npid = 0;
@@ -1350,31 +1373,37 @@ static ib_status build_stag_plan(ib_table* t, const std::vector<PlanOp>& ops, in
     // producer side: entries grouped by tile (counting sort keeps the pid order)
     std::vector<int32_t> eptr(ntiles + 1, 0), qptr(ntiles + 1, 0), emeta(nent), qpid;
     std::vector<T> ew(nent);
-    std::vector<int64_t> order(nent);
+    std::vector<int64_t> order(nent), tmp_order;
     for (int64_t i = 0; i < nent; ++i) eptr[ent[i].ptile + 1]++;
     for (int64_t tl = 0; tl < ntiles; ++tl) eptr[tl + 1] += eptr[tl];
     {
         std::vector<int32_t> fill(eptr.begin(), eptr.end() - 1);
         for (int64_t i = 0; i < nent; ++i) order[fill[ent[i].ptile]++] = i;
     }
+    std::vector<int32_t> pos(nent), rcount;
     int max_q = 0;
     for (int64_t tl = 0; tl < ntiles; ++tl) {
         const int64_t i0 = eptr[tl], i1 = eptr[tl + 1];
         qptr[tl] = (int32_t)qpid.size();
         const int64_t q0 = (int64_t)qpid.size();
-        for (int64_t i = i0; i < i1; ++i)
+        int32_t maxr = 0;
+        for (int64_t i = i0; i < i1; ++i) {
             if ((int64_t)qpid.size() == q0 || qpid.back() != pid[order[i]]) qpid.push_back(pid[order[i]]);
+            pos[order[i]] = (int32_t)((int64_t)qpid.size() - 1 - q0);
+            maxr = std::max(maxr, rank[order[i]]);
+        }
         max_q = std::max(max_q, (int)((int64_t)qpid.size() - q0));
-        // within the tile: by rank, then pid (adjacent lanes add into different partial sums)
-        std::sort(order.begin() + i0, order.begin() + i1, [&](int64_t x, int64_t y) {
-            return rank[x] != rank[y] ? rank[x] < rank[y] : pid[x] < pid[y];
-        });
+        // within the tile: by rank, then pid (a stable counting sort by rank of the
+        // pid-ordered entries), so adjacent lanes add into different partial sums
+        rcount.assign(maxr + 2, 0);
+        for (int64_t i = i0; i < i1; ++i) rcount[rank[order[i]] + 1]++;
+        for (int32_t r = 0; r <= maxr; ++r) rcount[r + 1] += rcount[r];
+        tmp_order.resize(i1 - i0);
+        for (int64_t i = i0; i < i1; ++i) tmp_order[rcount[rank[order[i]]]++] = order[i];
         for (int64_t k = i0; k < i1; ++k) {
-            const Ent& e = ent[order[k]];
-            const int32_t pos = (int32_t)(std::lower_bound(qpid.begin() + q0, qpid.end(), pid[order[k]]) -
-                                          (qpid.begin() + q0));
-            emeta[k] = (int32_t)((uint32_t)e.field << 31 | (uint32_t)pos << 11 | (uint32_t)e.slot);
-            ew[k] = (T)e.w;
+            const int64_t e = tmp_order[k - i0];
+            emeta[k] = (int32_t)((uint32_t)ent[e].field << 31 | (uint32_t)pos[e] << 11 | (uint32_t)ent[e].slot);
+            ew[k] = (T)ent[e].w;
         }
     }
     qptr[ntiles] = (int32_t)qpid.size();
