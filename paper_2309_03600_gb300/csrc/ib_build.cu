@@ -690,6 +690,51 @@ __device__ void qr_panel(const FitSmem& S, int ncol) {
     }
 }
 
+// Gram matrix of the fit, streamed over panels: G += B^T B (upper triangle of G,
+// kept in S.R).  Every (i, j) pair is owned by one thread, so a panel needs no
+// block-wide step per column.
+__device__ void gram_panel(const FitSmem& S, int ncol) {
+    const int np = ncol * (ncol + 1) / 2;
+    for (int p = threadIdx.x; p < np; p += blockDim.x) {
+        int i = 0, rem = p;                         // p -> (i, j), i <= j, row by row
+        while (rem >= ncol - i) {
+            rem -= ncol - i;
+            ++i;
+        }
+        const int j = i + rem;
+        double a = 0.0;
+#pragma unroll 8
+        for (int r = 0; r < FIT_PB; ++r) a += S.B[r * ncol + i] * S.B[r * ncol + j];
+        S.R[i * ncol + j] += a;
+    }
+}
+
+// Upper Cholesky factor R of G in place (R^T R = G = A^T A, so R has A's
+// singular values).  A non-positive pivot (columns dependent at working
+// precision) leaves a zero diagonal and a zero row, which the rank test reads
+// as singular.
+__device__ void chol_upper(const FitSmem& S, int n) {
+    double* R = S.R;
+    for (int k = 0; k < n; ++k) {
+        if (threadIdx.x == 0) {
+            const double piv = R[k * n + k];
+            S.scald[0] = piv > 0.0 ? sqrt(piv) : 0.0;
+        }
+        __syncthreads();
+        const double rkk = S.scald[0];
+        const double inv = rkk > 0.0 ? 1.0 / rkk : 0.0;
+        for (int j = k + 1 + threadIdx.x; j < n; j += blockDim.x) R[k * n + j] *= inv;
+        if (threadIdx.x == 0) R[k * n + k] = rkk;
+        __syncthreads();
+        const int w = n - k - 1;
+        for (int q = threadIdx.x; q < w * w; q += blockDim.x) {
+            const int i = k + 1 + q / w, j = k + 1 + q % w;
+            if (j >= i) R[i * n + j] -= R[k * n + i] * R[k * n + j];
+        }
+        __syncthreads();
+    }
+}
+
 // warp-level triangular solves on R (row-major, upper), vector in shared memory
 __device__ void warp_solve_RT(const double* R, const double* invd, int n, double* x) {   // R^T w = x
     int lane = threadIdx.x & 31;
@@ -1230,14 +1275,18 @@ __global__ void __launch_bounds__(FIT_THREADS) k_fit(FitParams P) {
                     __syncthreads();
                 }
                 if (m < ncol) continue;
-                // ---- streamed Householder QR
+                // ---- R with R^T R = A^T A: Gram matrix streamed over panels (A is never
+                // stored), then its Cholesky factor.  The seminormal solve below and its
+                // FP64 refinement from the rebuilt rows of A recover the accuracy.
                 for (int i = threadIdx.x; i < ncol * ncol; i += blockDim.x) S.R[i] = 0.0;
                 __syncthreads();
                 for (int row0 = 0; row0 < m; row0 += FIT_PB) {
                     build_panel(P, od, S, nsup, nbcrow, m, row0, ncol);
                     __syncthreads();
-                    qr_panel(S, ncol);
+                    gram_panel(S, ncol);
+                    __syncthreads();
                 }
+                chol_upper(S, ncol);
                 // ---- rank test: sigma_min / sigma_max of R
                 for (int k = threadIdx.x; k < ncol; k += blockDim.x) {
                     double rkk = S.R[k * ncol + k];
