@@ -17,11 +17,13 @@
 //
 // The correction of a modified row is the minimum-norm solution y of
 // A^T y = u, u = sum_e w_e a(x_e - x0), restricted to interior rows; this is
-// (A^+)^T u.  With A = QR (Householder, streamed in panels so A is never
-// stored) y = A R^{-1} R^{-T} u -- the seminormal equations of the
-// minimum-norm problem -- followed by one refinement step.  rank(A) = ncol is
-// decided from sigma_min / sigma_max of R estimated by inverse and power
-// iteration.
+// (A^+)^T u.  With R^T R = A^T A (the Cholesky factor of the Gram matrix,
+// accumulated over panels of rows so A is never stored) y = A R^{-1} R^{-T} u
+// -- the seminormal equations of the minimum-norm problem -- followed by one
+// refinement step from the rows of A rebuilt in FP64.  rank(A) = ncol is
+// decided from sigma_min / sigma_max of R (A's singular values) estimated by
+// inverse and power iteration.  The Householder sweep below serves the
+// learned-row check, which needs the row space of the BC rows.
 #include <cuda_runtime.h>
 #include <cub/cub.cuh>
 #include <thrust/iterator/counting_iterator.h>
