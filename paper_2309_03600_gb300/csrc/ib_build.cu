@@ -870,7 +870,7 @@ __device__ float block_sum_f(float v, double* red) {
 // largest singular value of an upper-triangular M (row-major, FP64 in shared
 // memory) by power iteration on M^T M in FP32: the rank decision needs a few
 // digits, and GB300's FP64 pipe is the constructor's bottleneck
-__device__ float block_sigma_max(const double* M, int n, float* v, float* w, double* red, int iters) {
+__device__ float block_sigma_max(const float* M, int n, float* v, float* w, double* red, int iters) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) v[i] = 1.f + 0.01f * (float)(i % 5);
     __syncthreads();
     float t0 = 0.f;
@@ -882,14 +882,14 @@ __device__ float block_sigma_max(const double* M, int n, float* v, float* w, dou
     for (int it = 0; it < iters; ++it) {
         for (int i = threadIdx.x; i < n; i += blockDim.x) {
             float t = 0.f;
-            for (int j = i; j < n; ++j) t += (float)M[i * n + j] * v[j];
+            for (int j = i; j < n; ++j) t += M[i * n + j] * v[j];
             w[i] = t;
         }
         __syncthreads();
         float t2 = 0.f;
         for (int j = threadIdx.x; j < n; j += blockDim.x) {
             float t = 0.f;
-            for (int i = 0; i <= j; ++i) t += (float)M[i * n + j] * w[i];
+            for (int i = 0; i <= j; ++i) t += M[i * n + j] * w[i];
             v[j] = t;
             t2 += t * t;
         }
@@ -1306,8 +1306,17 @@ __global__ void __launch_bounds__(FIT_THREADS) k_fit(FitParams P) {
                         tri_inverse(S.R, S.invd, S.X, ncol);
                         __syncthreads();
                         float* fv = (float*)S.vec;          // 2 * ncm floats in vec[0 .. ncm)
-                        float smax = block_sigma_max(S.R, ncol, fv, fv + ncm, S.scald + 4, 30);
-                        float sinv = block_sigma_max(S.X, ncol, fv, fv + ncm, S.scald + 4, 30);
+                        // FP32 copies in the (now free) panel buffer: ncol^2 floats fit in
+                        // FIT_PB * ncm doubles for ncm <= 64, and one conversion per
+                        // element keeps the FP64 pipe out of the iterations
+                        float* fm = (float*)S.B;
+                        for (int i = threadIdx.x; i < ncol * ncol; i += blockDim.x) fm[i] = (float)S.R[i];
+                        __syncthreads();
+                        float smax = block_sigma_max(fm, ncol, fv, fv + ncm, S.scald + 4, 30);
+                        __syncthreads();
+                        for (int i = threadIdx.x; i < ncol * ncol; i += blockDim.x) fm[i] = (float)S.X[i];
+                        __syncthreads();
+                        float sinv = block_sigma_max(fm, ncol, fv, fv + ncm, S.scald + 4, 30);
                         ratio = (smax > 0.f && sinv > 0.f && sinv < 3e38f) ? 1.0 / ((double)smax * (double)sinv) : 0.0;
                     } else {
                         if (threadIdx.x < 32) {
