@@ -832,6 +832,71 @@ __device__ double warp_cond_ratio(const double* R, const double* invd, int n, do
     return sqrt((double)smin2 / (double)smax2);
 }
 
+// The same estimate from an FP32 copy of R packed by rows (upper triangle):
+// element (i, j), j >= i, at rs(i) + j - i with rs(i) = i (2n - i + 1) / 2.
+__device__ __forceinline__ int packed_rs(int i, int n) { return i * (2 * n - i + 1) / 2; }
+__device__ double warp_cond_ratio_packed(const float* Rp, const float* invf, int n, double* xd, double* yd) {
+    const int lane = threadIdx.x & 31;
+    float* x = (float*)xd;
+    float* y = (float*)yd;
+    for (int i = lane; i < n; i += 32) x[i] = rsqrtf((float)n);
+    __syncwarp();
+    float smax2 = 0.f;
+    for (int it = 0; it < 24; ++it) {
+        for (int i = lane; i < n; i += 32) {
+            const float* row = Rp + packed_rs(i, n) - i;
+            float s = 0.f;
+            for (int j = i; j < n; ++j) s += row[j] * x[j];
+            y[i] = s;
+        }
+        __syncwarp();
+        for (int j = lane; j < n; j += 32) {
+            float s = 0.f;
+            int rs = 0;
+            for (int i = 0; i <= j; ++i) {
+                s += Rp[rs + j - i] * y[i];
+                rs += n - i;
+            }
+            x[j] = s;
+        }
+        __syncwarp();
+        const float nr = warp_norm_f(x, n);
+        if (!(nr > 0.f) || !(nr < 3e38f)) return 0.0;
+        smax2 = nr;
+        for (int i = lane; i < n; i += 32) x[i] /= nr;
+        __syncwarp();
+    }
+    for (int i = lane; i < n; i += 32) x[i] = rsqrtf((float)n) * (1.f + 0.01f * (float)(i % 7));
+    __syncwarp();
+    const float nx0 = warp_norm_f(x, n);
+    for (int i = lane; i < n; i += 32) x[i] /= nx0;
+    __syncwarp();
+    float smin2 = 0.f;
+    for (int it = 0; it < 40; ++it) {
+        for (int k = 0; k < n; ++k) {
+            const float wk = x[k] * invf[k];
+            __syncwarp();
+            if (lane == 0) x[k] = wk;
+            const float* row = Rp + packed_rs(k, n) - k;
+            for (int i = k + 1 + lane; i < n; i += 32) x[i] -= row[i] * wk;
+            __syncwarp();
+        }
+        for (int k = n - 1; k >= 0; --k) {
+            const float yk = x[k] * invf[k];
+            __syncwarp();
+            if (lane == 0) x[k] = yk;
+            for (int i = lane; i < k; i += 32) x[i] -= Rp[packed_rs(i, n) + k - i] * yk;
+            __syncwarp();
+        }
+        const float nr = warp_norm_f(x, n);
+        if (!(nr < 3e38f) || nr == 0.f) return 0.0;
+        smin2 = 1.f / nr;
+        for (int i = lane; i < n; i += 32) x[i] /= nr;
+        __syncwarp();
+    }
+    return sqrt((double)smin2 / (double)smax2);
+}
+
 // X = R^{-1} (upper triangular): thread j back-substitutes column j
 __device__ void tri_inverse(const double* R, const double* invd, double* X, int n) {
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
@@ -1319,8 +1384,21 @@ __global__ void __launch_bounds__(FIT_THREADS) k_fit(FitParams P) {
                         float sinv = block_sigma_max(fm, ncol, fv, fv + ncm, S.scald + 4, 30);
                         ratio = (smax > 0.f && sinv > 0.f && sinv < 3e38f) ? 1.0 / ((double)smax * (double)sinv) : 0.0;
                     } else {
+                        // packed FP32 copy of R (and 1/R_kk) in the free panel buffer when it fits
+                        const int npk = ncol * (ncol + 1) / 2;
+                        const bool packed = (npk + ncol) * 4 <= FIT_PB * ncm * 8;
+                        float* rp = (float*)S.B;
+                        if (packed) {
+                            for (int i = threadIdx.x; i < ncol; i += blockDim.x) {
+                                const int rs = packed_rs(i, ncol) - i;
+                                for (int j = i; j < ncol; ++j) rp[rs + j] = (float)S.R[i * ncol + j];
+                                rp[npk + i] = (float)S.invd[i];
+                            }
+                            __syncthreads();
+                        }
                         if (threadIdx.x < 32) {
-                            double rr = warp_cond_ratio(S.R, S.invd, ncol, S.vec, S.vec + ncm);
+                            double rr = packed ? warp_cond_ratio_packed(rp, rp + npk, ncol, S.vec, S.vec + ncm)
+                                               : warp_cond_ratio(S.R, S.invd, ncol, S.vec, S.vec + ncm);
                             if (threadIdx.x == 0) S.scald[4] = rr;
                         }
                         __syncthreads();
