@@ -105,10 +105,20 @@ __device__ __forceinline__ void seg_add(T* acc, int32_t loc, T val, bool valid, 
 }
 
 template <typename T>
+__device__ __forceinline__ void add_entries_range(const TileView<T>& v, int32_t e0, int32_t e1, const T* f,
+                                                  int64_t origin, T* acc, int tid, int nthr);
+
+template <typename T>
 __device__ __forceinline__ void add_entries(const TileView<T>& v, int64_t tile, const T* f, int64_t origin, T* acc,
                                             int tid, int nthr) {
+    add_entries_range(v, v.ptr[tile], v.ptr[tile + 1], f, origin, acc, tid, nthr);
+}
+
+// entries [e0, e1) of a tile (the range read ahead by the caller)
+template <typename T>
+__device__ __forceinline__ void add_entries_range(const TileView<T>& v, int32_t e0, int32_t e1, const T* f,
+                                                  int64_t origin, T* acc, int tid, int nthr) {
     constexpr int U = 4;
-    const int32_t e0 = v.ptr[tile], e1 = v.ptr[tile + 1];
     const int lane = tid & 31;
     const int32_t warp_base = (tid & ~31) * U;
     const int32_t step = nthr * U;
@@ -422,9 +432,25 @@ __global__ void __launch_bounds__(256) k_leap3d_tma(StepArgs<float> a, const __g
     int64_t qi = L.idx(x, y, zb);
     float pm_n = valid ? a.pm[qi] : 0.f;
     float kh_n = valid ? a.Kh[qi] : 0.f;
+    // read ahead: the correction range of the next tile plane, and this thread's source corner
+    const int64_t tile_z = nty * a.op.ntx;                  // tiles per plane
+    const int64_t tile0 = (int64_t)blockIdx.y * a.op.ntx + blockIdx.x;
+    int32_t e0n = 0, e1n = 0;
+    if (a.op.ptr) {
+        e0n = a.op.ptr[zb * tile_z + tile0];
+        e1n = a.op.ptr[zb * tile_z + tile0 + 1];
+    }
+    const bool src_me = tid < 8 * a.src.n;
+    const int64_t s_idx = src_me ? a.src.idx[tid] : 0;
+    const float s_w = src_me ? a.src.w[tid] : 0.f;
     for (int64_t z = zb; z < ze; ++z) {
         const int it = (int)(z - zb);
         const int st = it % NS, sf = (it + H) % NS;
+        const int32_t e0 = e0n, e1 = e1n;
+        if (a.op.ptr && z + 1 < ze) {
+            e0n = a.op.ptr[(z + 1) * tile_z + tile0];
+            e1n = a.op.ptr[(z + 1) * tile_z + tile0 + 1];
+        }
         bool ok = mbar_wait_bounded(&bar[st], (uint32_t)((it / NS) & 1));
         ok = ok && mbar_wait_bounded(&bar[sf], (uint32_t)(((it + H) / NS) & 1));
         if (__syncthreads_or(!ok)) {
@@ -454,8 +480,14 @@ __global__ void __launch_bounds__(256) k_leap3d_tma(StepArgs<float> a, const __g
         }
         const int64_t origin = L.idx(x0, y0, z);
         __syncthreads();
-        tile_sources<float, TX, TY>(a.src, wv, origin, L.px, sadd, tid);
-        if (a.op.ptr) add_entries(a.op, (z * nty + blockIdx.y) * a.op.ntx + blockIdx.x, a.p, origin, acc, tid, 256);
+        if (src_me && s_w != 0.f) {
+            const int64_t rel = s_idx - origin;
+            if (rel >= 0) {
+                const int64_t ly = rel / L.px, lx = rel - ly * L.px;
+                if (ly < TY && lx < TX) atomicAdd(&sadd[ly * TX + lx], s_w * wv);
+            }
+        }
+        if (e1 > e0) add_entries_range(a.op, e0, e1, a.p, origin, acc, tid, 256);
         __syncthreads();
         if (valid) {
             const float c = q[H];
