@@ -386,7 +386,7 @@ struct Tma3D {
     static constexpr int TX = 32, TY = 8;
     static constexpr int BW = TX + 8;         // x halo 4 on each side (16-byte aligned box)
     static constexpr int BH = TY + 2 * H;
-    static constexpr int NS = H + 3;          // ring slots: planes z .. z + H + 2
+    static constexpr int NS = H + 6;          // ring slots: planes z .. z + H + 5 (5 planes in flight)
     static constexpr uint32_t BYTES = BW * BH * 4;
     static constexpr int SLOT = (BW * BH + 31) / 32 * 32;   // slot stride in floats (128-byte multiple)
 };
@@ -429,9 +429,14 @@ __global__ void __launch_bounds__(256) k_leap3d_tma(StepArgs<float> a, const __g
 #pragma unroll
     for (int k = 0; k < 2 * H; ++k) q[k] = col_ok ? a.p[L.idx(x, y, zb - H + k)] : 0.f;
     const float wv = a.src.n ? a.wavelet[a.step] : 0.f;
+    // p_prev and Kh are read two planes ahead of use
     int64_t qi = L.idx(x, y, zb);
-    float pm_n = valid ? a.pm[qi] : 0.f;
-    float kh_n = valid ? a.Kh[qi] : 0.f;
+    float pm_a = valid ? a.pm[qi] : 0.f, kh_a = valid ? a.Kh[qi] : 0.f;
+    float pm_b = 0.f, kh_b = 0.f;
+    if (valid && zb + 1 < ze) {
+        pm_b = a.pm[qi + L.plane];
+        kh_b = a.Kh[qi + L.plane];
+    }
     // read ahead: the correction range of the next tile plane, and this thread's source corner
     const int64_t tile_z = nty * a.op.ntx;                  // tiles per plane
     const int64_t tile0 = (int64_t)blockIdx.y * a.op.ntx + blockIdx.x;
@@ -457,14 +462,16 @@ __global__ void __launch_bounds__(256) k_leap3d_tma(StepArgs<float> a, const __g
             if (tid == 0) atomicExch(err, 1);
             return;
         }
-        // software pipeline: next plane's p_prev and Kh
-        const float pm_c = pm_n, kh_c = kh_n;
+        // software pipeline: p_prev and Kh of plane z + 2
+        const float pm_c = pm_a, kh_c = kh_a;
         const int64_t qc = qi;
-        if (z + 1 < ze) {
-            qi += L.plane;
-            pm_n = valid ? a.pm[qi] : 0.f;
-            kh_n = valid ? a.Kh[qi] : 0.f;
+        pm_a = pm_b;
+        kh_a = kh_b;
+        if (valid && z + 2 < ze) {
+            pm_b = a.pm[qi + 2 * L.plane];
+            kh_b = a.Kh[qi + 2 * L.plane];
         }
+        qi += L.plane;
         const float* rt = ring + st * SLOT;          // plane z, row j <-> y0 - H + j
         q[2 * H] = ring[sf * SLOT + (H + ty) * BW + 4 + tx];
         sadd[tid] = 0.f;
