@@ -82,6 +82,21 @@ def make_workload(name, bc, rank=0, nt=0, grid=None):
     return w
 
 
+def max_over_ranks(ms, dist, device):
+    """Step time of the whole job: the slowest rank's, returned on every rank."""
+    if not dist:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, units_per_rank, ms):
+    """Whole-job throughput: the units all ranks processed over the slowest rank's step time."""
+    return world * units_per_rank / (ms * 1e-3)
+
+
 def grid_points(w):
     n = 1
     for v in w["shape"]:
@@ -361,14 +376,10 @@ def main():
     prof = ib.ib_profile()
     stats = tab.stats()
     ms_steps = [a.elapsed_time(b) for a, b in ev]
-    ms = sum(ms_steps) / len(ms_steps)
-    if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(sum(ms_steps) / len(ms_steps), dist, dev)
     N = grid_points(w)
     upd_per_step = N * nt
-    value = world * upd_per_step / (ms * 1e-3)
+    value = job_value(world, upd_per_step, ms)
     launches = sum(d["launches"] for d in prof.values())
     # ---- roofline of the dominant kernel
     kb = kernel_bytes(w, stats, eb)
@@ -411,8 +422,8 @@ def main():
             traces_h.copy_(tr, non_blocking=True)
             torch.cuda.synchronize()
             e2e_ms.append(1e3 * (time.perf_counter() - t0))
-        em = sum(e2e_ms) / len(e2e_ms)
-        e2e = {"value": world * upd_per_step / (em * 1e-3), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+        em = max_over_ranks(sum(e2e_ms) / len(e2e_ms), dist, dev)
+        e2e = {"value": job_value(world, upd_per_step, em), "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(traces_h.numel() * traces_h.element_size()), "ms_per_step": em}
     # ---- CPU oracle baseline (rank 0, one GPU)
     cpu = None
@@ -541,11 +552,7 @@ def run_learned(args, world, rank, local, dev, dist):
         dist.barrier()
     clk = clocks.stop()
     prof = ib.ib_profile()
-    ms = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
-    if dist:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / len(ev), dist, dev)
     st = tab.stats()
     checked, accepted, res = ib.ib_table_learned(tab)
     fin = res[np.isfinite(res)] if res.size else res
@@ -573,7 +580,7 @@ def run_learned(args, world, rank, local, dev, dist):
     if rank != 0:
         return 0
     out = {
-        "metric": METRIC, "value": world * N * nt / (ms * 1e-3), "unit": UNIT, "n_gpus": world,
+        "metric": METRIC, "value": job_value(world, N * nt, ms), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": "learned3d", "desc": "3D second-order, %dx%dx%d, h=10 m, order 8, FP32, %d steps, "
@@ -665,12 +672,8 @@ def run_shots(args, world, rank, local, dev, dist):
         dist.barrier()
     clk = clocks.stop()
     prof = ib.ib_profile()
-    ms = sum(a.elapsed_time(b) for a, b in ev) / len(ev)
-    if dist:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
-    value = world * N * nt / (ms * 1e-3)
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / len(ev), dist, dev)
+    value = job_value(world, N * nt, ms)
     kernels = {k: {"launches": d["launches"], "avg_us": 1e3 * d["sampled_ms"] / d["sampled"]}
                for k, d in prof.items() if d["sampled"]}
     peak, peak_kind = peaks()
