@@ -285,3 +285,51 @@ def test_block_structure_coupling():
         for r in A[:n_int]:
             assert (np.abs(r[:T]).sum() == 0) != (np.abs(r[T:]).sum() == 0)
         assert all(np.abs(r[:T]).sum() > 0 and np.abs(r[T:]).sum() > 0 for r in A[n_int:])
+
+
+# ---------------------------------------------------------------------------
+# spatial convergence under grid refinement
+# ---------------------------------------------------------------------------
+def _flat_refinement_errors(M, bc, hs):
+    """Max |L_mod f - lap f| at IB rows and at interior rows for a field that
+    satisfies every imposed condition on the off-grid plane z = z0:
+    free  f = sin(k (z - z0)) cos(m x)  (f, lap f, lap^2 f, ... vanish there),
+    rigid f = cos(k (z - z0)) cos(m x)  (every normal derivative of odd order vanishes).
+    Rows within M/2 of the other array edges (zero halo) are left out."""
+    from oracle import operators
+    out = []
+    for h in hs:
+        n = int(round(1.0 / h)) + 1
+        z0 = 0.3037
+        geom = stencils.Geometry(inputs.flat_surface_sdf((n, n), h, z0), h, M)
+        L, rows = operators.laplacian_matrix(geom, bc, stencils.Opts(M))
+        X, Z = np.meshgrid(np.arange(n) * h, np.arange(n) * h)
+        k, m = 2 * np.pi * 1.3, 2 * np.pi * 0.9
+        f = (np.sin(k * (Z - z0)) if bc == "free" else np.cos(k * (Z - z0))) * np.cos(m * X)
+        f = np.where(geom.mask, f, 0.0)
+        err = np.abs((L @ f.ravel()).reshape(f.shape) + (k * k + m * m) * f)
+        H = M // 2
+        inner = geom.mask.copy()
+        inner[:, :H] = inner[:, n - H:] = inner[n - H:, :] = False
+        ib = np.zeros_like(inner)
+        for (i, j) in rows:
+            if H <= i < n - H:
+                ib[j, i] = True
+        inner &= ~ib
+        out.append((err[ib].max(), err[inner].max()))
+    return out
+
+
+@pytest.mark.parametrize("bc", ["free", "rigid"])
+@pytest.mark.parametrize("M", [4, 8])
+def test_spatial_convergence_flat_offgrid(bc, M):
+    """Interior rows converge at the stencil order M.  Modified rows converge
+    at the order of the extrapolation: a basis of order 4 leaves an O(h^5)
+    error in the extrapolated values, O(h^3) after the 1/h^2 of the second
+    derivative.  The surface sits at a different fraction of a cell on each
+    grid, so the modified rows are checked over two refinements together."""
+    e = _flat_refinement_errors(M, bc, (1 / 24, 1 / 48, 1 / 96))
+    for a, b in zip(e, e[1:]):
+        order = np.log2(a[1] / b[1])
+        assert M - 0.5 < order < M + 0.5, order
+    assert np.log2(e[0][0] / e[2][0]) / 2 > 2.5, e
