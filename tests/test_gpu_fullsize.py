@@ -1,0 +1,143 @@
+"""Parity at the benchmark's full sizes, in the launch configuration bench.py
+times: sampled table rows of the 1001 x 1001 staggered and the 512 x 512 x 384
+hills workloads against the oracle's fit of the same rows, and equalities of
+the timed kernels with their plain counterparts over whole runs.
+
+The oracle fits a sampled row on a crop of the full SDF around the row's node.
+A fit only sees the support (radius <= 5.5 grid units), the boundary points in
+it and the SDF normals at those points (central differences over +-M/2 nodes),
+so a crop of half-width 12 (3D) / 14 (2D) gives the same fit as the full array
+wherever the crop does not cut the array's own edge."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import stencils
+from paper_2309_03600_gb300 import inputs
+from gpu_util import compare_tables, cuda, gpu_rows, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+ib = pytest.importorskip("paper_2309_03600_gb300.ib")
+
+
+def _crop(full_shape, node, hw):
+    """Slices (array order) of a crop of half-width hw around node (logical
+    order) and the node's coordinates in the crop."""
+    sl, local = [], []
+    for a, n in enumerate(node):
+        ax = len(node) - 1 - a
+        lo = max(0, n - hw)
+        hi = min(full_shape[ax], n + hw + 1)
+        sl.append(slice(lo, hi))
+        local.append(n - lo)
+    return tuple(reversed(sl)), tuple(local)
+
+
+def _sample(rows, k, seed):
+    rng = np.random.default_rng(seed)
+    return sorted(rng.choice(len(rows), size=min(k, len(rows)), replace=False))
+
+
+@pytest.fixture(scope="module")
+def hills_full():
+    w = inputs.workload_hills3d(device="cuda")
+    sdf = torch.as_tensor(w["sdf"], dtype=torch.float64, device="cuda")
+    return w, sdf
+
+
+def test_hills3d_full_size_sampled_rows(hills_full):
+    w, sdf = hills_full
+    t = ib.ib_build_stencils(sdf, w["h"], "free", "second", w["M"])
+    ex = t.export(0)
+    shape = tuple(sdf.shape)
+    nrow = len(ex["row_node"])
+    assert nrow > 500000
+    picks = _sample(ex["row_node"], 24, 7)
+    # add grown rows (support beyond the first radius) when present
+    grown = np.nonzero(ex["info"][:, 0] != 5)[0]
+    picks += [int(r) for r in grown[:: max(1, len(grown) // 6)][:6]]
+    opts = stencils.Opts(w["M"])
+    for r in picks:
+        lin = int(ex["row_node"][r])
+        node = tuple(int(v) for v in reversed(np.unravel_index(lin, shape)))
+        sl, local = _crop(shape, node, 12)
+        crop = sdf[sl].cpu().numpy()
+        geom = stencils.Geometry(crop, w["h"], w["M"])
+        orc = stencils.laplacian_rows(geom, "free", opts, [local])
+        sub = {"row_node": np.array([0]), "row_ptr": np.array([0, ex["row_ptr"][r + 1] - ex["row_ptr"][r]]),
+               "col": ex["col"][ex["row_ptr"][r]:ex["row_ptr"][r + 1]],
+               "w": ex["w"][ex["row_ptr"][r]:ex["row_ptr"][r + 1]], "info": ex["info"][r:r + 1]}
+        gpu = gpu_rows(sub, crop.shape)
+        compare_tables({local: orc[local]}, {local: gpu[(0, 0, 0)]}, rtol=1e-8)
+
+
+def test_hills3d_full_size_tma_equals_plain_loads(hills_full, monkeypatch):
+    """The timed TMA kernel against the plain-load kernel on the full grid
+    (200 steps): the same arithmetic, so equal to FP32 summation order."""
+    w, sdf = hills_full
+    t = ib.ib_build_stencils(sdf, w["h"], "free", "second", w["M"])
+    vel = torch.as_tensor(w["vel"], dtype=torch.float32, device="cuda")
+    args = (vel, cuda(w["wavelet"][:200], torch.float32), cuda(w["src"]), cuda(w["rec"]), w["dt"], 200)
+    a = ib.ib_forward(t, *args).double().cpu().numpy()
+    monkeypatch.setenv("IB_NO_TMA", "1")
+    b = ib.ib_forward(t, *args).double().cpu().numpy()
+    assert np.isfinite(a).all() and np.abs(a).max() > 0
+    assert rel_l2(a, b) < 1e-6
+
+
+@pytest.fixture(scope="module")
+def stag_full():
+    w = inputs.workload_sinusoid_staggered(bc="free", seed=2)
+    return w, cuda(w["sdf"])
+
+
+def test_stag2d_full_size_sampled_rows(stag_full):
+    w, sdf = stag_full
+    t = ib.ib_build_stencils(sdf, w["h"], "free", "staggered", w["M"])
+    shape = tuple(sdf.shape)
+    opts = stencils.Opts(w["M"])
+    exs = [t.export(o) for o in range(4)]
+    for op in (0, 1, 2):
+        ex = exs[op]
+        for r in _sample(ex["row_node"], 12, 11 + op):
+            node = tuple(int(v) for v in reversed(np.unravel_index(int(ex["row_node"][r]), shape)))
+            sl, local = _crop(shape, node, 14)
+            crop = w["sdf"][sl]
+            geom = stencils.Geometry(crop, w["h"], w["M"])
+            if op < 2:
+                orc = stencils.gradient_rows(geom, op, "free", opts, [local])
+                parts = [(exs[op], None)]
+            else:
+                orc = stencils.divergence_rows(geom, "free", opts, [local])
+                parts = [(exs[2], 0), (exs[3], 1)]
+            merged = None
+            for e, comp in parts:
+                rr = np.nonzero(e["row_node"] == ex["row_node"][r])[0]
+                if len(rr) == 0:
+                    continue
+                k = int(rr[0])
+                sub = {"row_node": np.array([0]), "row_ptr": np.array([0, e["row_ptr"][k + 1] - e["row_ptr"][k]]),
+                       "col": e["col"][e["row_ptr"][k]:e["row_ptr"][k + 1]],
+                       "w": e["w"][e["row_ptr"][k]:e["row_ptr"][k + 1]], "info": e["info"][k:k + 1]}
+                g = gpu_rows(sub, crop.shape, comp_prefix=comp)[(0, 0)]
+                merged = g if merged is None else ({**merged[0], **g[0]}, merged[1])
+            compare_tables({local: orc[local]}, {local: merged}, rtol=1e-8)
+
+
+def test_stag2d_full_size_graph_equals_plain_launches(stag_full, monkeypatch):
+    """The timed 50-step graph replays against one launch per kernel over the
+    full 3000 steps.  Both run the same kernels in the same order; the IB
+    partial sums use shared-memory atomics, whose order varies from run to run,
+    and over 3000 steps that FP32 rounding reaches ~1e-6 relative.  The bound is
+    the FP32 trace tolerance of the method."""
+    w, sdf = stag_full
+    t = ib.ib_build_stencils(sdf, w["h"], "free", "staggered", w["M"])
+    args = (cuda(w["vel"], torch.float32), cuda(w["wavelet"], torch.float32), cuda(w["src"]), cuda(w["rec"]),
+            w["dt"], w["nt"])
+    rho = cuda(w["rho"], torch.float32)
+    a = ib.ib_forward(t, *args, rho=rho).double().cpu().numpy()
+    monkeypatch.setenv("IB_NO_GRAPH", "1")
+    b = ib.ib_forward(t, *args, rho=rho).double().cpu().numpy()
+    assert np.isfinite(a).all() and np.abs(a).max() > 0
+    assert rel_l2(a, b) < 1e-5

@@ -10,7 +10,8 @@ from paper_2309_03600_gb300 import inputs
 from gpu_util import compare_tables, cuda, gpu_rows, rel_l2
 
 # FP64 traces: the library's weights come from its own FP64 factorisation
-# (streamed Householder QR, seminormal equations + one refinement) of the same
+# (Cholesky factor of the streamed Gram matrix, seminormal equations + one
+# refinement) of the same
 # A that the oracle pseudo-inverts by SVD; the two agree to ~1e-13 cond(A)
 # (table tests), which bounds the FP64 trace difference well below 1e-7.
 TOL64 = 1e-7
