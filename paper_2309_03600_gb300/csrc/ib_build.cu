@@ -758,12 +758,6 @@ __device__ void warp_solve_R(const double* R, const double* invd, int n, double*
         __syncwarp();
     }
 }
-__device__ double warp_norm(const double* x, int n) {
-    double s = 0.0;
-    for (int i = threadIdx.x & 31; i < n; i += 32) s += x[i] * x[i];
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    return sqrt(s);
-}
 
 // sigma_min / sigma_max of R by power / inverse iteration in one warp (large n)
 // sigma_min / sigma_max of R by power and inverse iteration in one warp, in
