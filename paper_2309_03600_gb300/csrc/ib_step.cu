@@ -188,20 +188,52 @@ struct StepArgs {
     int64_t ntiles;      // tiles of the shot (blocks beyond only record receivers)
 };
 
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// asynchronous global -> shared copy of B bytes (zero fill when !valid)
+template <int B>
+__device__ __forceinline__ void cp_async(void* dst, const void* src, bool valid) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(smem_u32(dst)), "l"(src), "n"(B),
+                 "r"(valid ? B : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 template <typename T, int H, int TX, int TZ>
 __device__ __forceinline__ void leap2d_tile(const StepArgs<T>& a, int64_t bx, int64_t bz, T (*tile)[TX + 2 * H],
                                             T* acc, T* sadd) {
+    static_assert((TZ * TX) % 256 == 0, "whole points per thread");
+    constexpr int PT = TZ * TX / 256;
     const int tid = threadIdx.x;
-    for (int i = tid; i < TZ * TX; i += 256) sadd[i] = (T)0;
     const int64_t x0 = bx * TX, z0 = bz * TZ;
     const Layout& L = a.L;
+    // the halo tile arrives by cp.async (zero fill past the padded array) ...
     for (int i = tid; i < (TZ + 2 * H) * (TX + 2 * H); i += 256) {
-        int lz = i / (TX + 2 * H), lx = i - lz * (TX + 2 * H);
-        int64_t x = x0 + lx - H, z = z0 + lz - H;
-        T v = 0;
-        if (x < L.nx + H && z < L.nz + H) v = a.p[L.base + z * L.px + x];
-        tile[lz][lx] = v;
+        const int lz = i / (TX + 2 * H), lx = i - lz * (TX + 2 * H);
+        const int64_t x = x0 + lx - H, z = z0 + lz - H;
+        const bool ok = x < L.nx + H && z < L.nz + H;
+        cp_async<(int)sizeof(T)>(&tile[lz][lx], ok ? a.p + L.base + z * L.px + x : a.p, ok);
     }
+    cp_async_commit();
+    for (int i = tid; i < TZ * TX; i += 256) sadd[i] = (T)0;
+    // ... while this thread's p_prev and K, and the tile's correction range, load
+    const int64_t origin = L.base + z0 * L.px + x0;
+    T pmv[PT], khv[PT];
+#pragma unroll
+    for (int j = 0; j < PT; ++j) {
+        const int i = tid + 256 * j, lz = i / TX, lx = i - lz * TX;
+        const bool in = x0 + lx < L.nx && z0 + lz < L.nz;
+        const int64_t q = origin + lz * L.px + lx;
+        pmv[j] = in ? a.pm[q] : (T)0;
+        khv[j] = in ? a.Kh[q] : (T)0;
+    }
+    int32_t e0 = 0, e1 = 0;
+    if (a.op.ptr) {
+        e0 = a.op.ptr[bz * a.op.ntx + bx];
+        e1 = a.op.ptr[bz * a.op.ntx + bx + 1];
+    }
+    cp_async_wait_all();
     __syncthreads();
     // Laplacian in difference form, sum_k w_k sum_axes (p_{+k} - p_0 + p_{-k} - p_0): the
     // discrete operator annihilates constants exactly in floating point (row sum zero)
@@ -215,19 +247,18 @@ __device__ __forceinline__ void leap2d_tile(const StepArgs<T>& a, int64_t bx, in
                             ((tile[lz + H + k][lx + H] - c) + (tile[lz + H - k][lx + H] - c)));
         acc[i] = s;
     }
-    const int64_t origin = L.base + z0 * L.px + x0;
     const T wv = a.src.n ? a.wavelet[a.step] : (T)0;
     tile_sources<T, TX, TZ>(a.src, wv, origin, L.px, sadd, tid);
     __syncthreads();
-    if (a.op.ptr) add_entries(a.op, bz * a.op.ntx + bx, a.p, origin, acc, tid, 256);
+    if (e1 > e0) add_entries_range(a.op, e0, e1, a.p, origin, acc, tid, 256);
     __syncthreads();
-    for (int i = tid; i < TZ * TX; i += 256) {
-        int lz = i / TX, lx = i - lz * TX;
-        int64_t x = x0 + lx, z = z0 + lz;
-        if (x >= L.nx || z >= L.nz) continue;
-        int64_t q = origin + lz * L.px + lx;
-        T c = tile[lz + H][lx + H];
-        a.out[q] = c + ((c - a.pm[q]) + a.Kh[q] * acc[i]) + sadd[i];
+#pragma unroll
+    for (int j = 0; j < PT; ++j) {
+        const int i = tid + 256 * j, lz = i / TX, lx = i - lz * TX;
+        if (x0 + lx >= L.nx || z0 + lz >= L.nz) continue;
+        const int64_t q = origin + lz * L.px + lx;
+        const T c = tile[lz + H][lx + H];
+        a.out[q] = c + ((c - pmv[j]) + khv[j] * acc[i]) + sadd[i];
     }
 }
 
@@ -244,17 +275,13 @@ __global__ void __launch_bounds__(256) k_leap2d(StepArgs<T> a) {
 // many shots in one launch: block -> (shot, tile) through the per-shot tile offsets
 template <typename T, int H, int TX, int TZ>
 __global__ void __launch_bounds__(256) k_leap2d_batch(const StepArgs<T>* __restrict__ shots,
-                                                      const int64_t* __restrict__ tile0, int nshot, int step) {
+                                                      const int64_t* __restrict__ tile0,
+                                                      const int32_t* __restrict__ shot_of, int nshot, int step) {
     __shared__ T tile[TZ + 2 * H][TX + 2 * H];
     __shared__ T acc[TZ * TX];
     __shared__ T sadd[TZ * TX];
     const int64_t b = blockIdx.x;
-    int lo = 0, hi = nshot - 1;
-    while (lo < hi) {                     // last shot with tile0[s] <= b
-        int mid = (lo + hi + 1) >> 1;
-        if (tile0[mid] <= b) lo = mid;
-        else hi = mid - 1;
-    }
+    const int lo = shot_of[b];            // the shot whose tiles include block b
     StepArgs<T> a = shots[lo];
     const int64_t local = b - tile0[lo];
     T* cur = (step & 1) ? a.buf1 : a.buf0;
@@ -346,7 +373,6 @@ __global__ void __launch_bounds__(256) k_leap3d(StepArgs<T> a, int zchunk, int64
 // register queue fed by the centre of plane z + H.  Every wait is bounded: on
 // timeout the block records an error and leaves.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
@@ -572,16 +598,6 @@ struct StagArgs {
     int nt;
     int rec_step;
 };
-
-// asynchronous global -> shared copy of B bytes (zero fill when !valid)
-template <int B>
-__device__ __forceinline__ void cp_async(void* dst, const void* src, bool valid) {
-    asm volatile("cp.async.ca.shared.global [%0], [%1], %2, %3;\n" ::"r"(smem_u32(dst)), "l"(src), "n"(B),
-                 "r"(valid ? B : 0)
-                 : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
 
 // consumer side: correction of row i of this tile's list = sum of its partials
 template <typename T>
@@ -1874,29 +1890,32 @@ struct TileShape {
 static const TileShape kShapes[4] = {{64, 8}, {32, 16}, {128, 4}, {64, 4}};
 
 template <int H, int TX, int TZ>
-static void launch_batch(const StepArgs<float>* args, const int64_t* tile0, int nshot, int step, int64_t nblk,
+static void launch_batch(const StepArgs<float>* args, const int64_t* tile0, const int32_t* shot_of, int nshot,
+                         int step, int64_t nblk,
                          cudaStream_t s) {
-    k_leap2d_batch<float, H, TX, TZ><<<(unsigned)nblk, 256, 0, s>>>(args, tile0, nshot, step);
+    k_leap2d_batch<float, H, TX, TZ><<<(unsigned)nblk, 256, 0, s>>>(args, tile0, shot_of, nshot, step);
 }
 
 template <int H>
-static void launch_batch_shape(int si, const StepArgs<float>* args, const int64_t* tile0, int nshot, int step,
+static void launch_batch_shape(int si, const StepArgs<float>* args, const int64_t* tile0, const int32_t* shot_of,
+                               int nshot, int step,
                                int64_t nblk, cudaStream_t s) {
     switch (si) {
-        case 0: launch_batch<H, 64, 8>(args, tile0, nshot, step, nblk, s); break;
-        case 1: launch_batch<H, 32, 16>(args, tile0, nshot, step, nblk, s); break;
-        case 2: launch_batch<H, 128, 4>(args, tile0, nshot, step, nblk, s); break;
-        default: launch_batch<H, 64, 4>(args, tile0, nshot, step, nblk, s); break;
+        case 0: launch_batch<H, 64, 8>(args, tile0, shot_of, nshot, step, nblk, s); break;
+        case 1: launch_batch<H, 32, 16>(args, tile0, shot_of, nshot, step, nblk, s); break;
+        case 2: launch_batch<H, 128, 4>(args, tile0, shot_of, nshot, step, nblk, s); break;
+        default: launch_batch<H, 64, 4>(args, tile0, shot_of, nshot, step, nblk, s); break;
     }
 }
 
-static void launch_batch_any(int H, int si, const StepArgs<float>* args, const int64_t* tile0, int nshot, int step,
+static void launch_batch_any(int H, int si, const StepArgs<float>* args, const int64_t* tile0, const int32_t* shot_of,
+                             int nshot, int step,
                              int64_t nblk, cudaStream_t s) {
     PROF_LAUNCH("leap2d_batch_f32", s, {
-        if (H == 1) launch_batch_shape<1>(si, args, tile0, nshot, step, nblk, s);
-        else if (H == 2) launch_batch_shape<2>(si, args, tile0, nshot, step, nblk, s);
-        else if (H == 3) launch_batch_shape<3>(si, args, tile0, nshot, step, nblk, s);
-        else launch_batch_shape<4>(si, args, tile0, nshot, step, nblk, s);
+        if (H == 1) launch_batch_shape<1>(si, args, tile0, shot_of, nshot, step, nblk, s);
+        else if (H == 2) launch_batch_shape<2>(si, args, tile0, shot_of, nshot, step, nblk, s);
+        else if (H == 3) launch_batch_shape<3>(si, args, tile0, shot_of, nshot, step, nblk, s);
+        else launch_batch_shape<4>(si, args, tile0, shot_of, nshot, step, nblk, s);
     });
 }
 
@@ -1908,6 +1927,7 @@ struct BatchSetup {
     std::vector<int64_t> tile0;
     StepArgs<float>* d_args = nullptr;
     int64_t* d_tile0 = nullptr;
+    int32_t* d_shot_of = nullptr;   // shot of each block
     int64_t nblk = 0;
 };
 
@@ -1949,6 +1969,12 @@ static ib_status batch_prepare(ib_table* const* ts, const ib_shot* shots, int ns
     TRY(S.alloc(&B.d_tile0, nshot + 1));
     IB_CUDA(cudaMemcpyAsync(B.d_args, B.args.data(), sizeof(StepArgs<float>) * nshot, cudaMemcpyHostToDevice, S.s));
     IB_CUDA(cudaMemcpyAsync(B.d_tile0, B.tile0.data(), 8 * (nshot + 1), cudaMemcpyHostToDevice, S.s));
+    std::vector<int32_t> shot_of(B.nblk);
+    for (int i = 0; i < nshot; ++i)
+        for (int64_t b = B.tile0[i]; b < B.tile0[i + 1]; ++b) shot_of[b] = i;
+    TRY(S.alloc(&B.d_shot_of, std::max<int64_t>(B.nblk, 1)));
+    IB_CUDA(cudaMemcpyAsync(B.d_shot_of, shot_of.data(), 4 * B.nblk, cudaMemcpyHostToDevice, S.s));
+    IB_CUDA(cudaStreamSynchronize(S.s));   // the host table goes out of scope
     return IB_OK;
 }
 
@@ -2018,9 +2044,9 @@ extern "C" ib_status ib_forward_batch(const ib_table* const* tables, const ib_sh
                 BatchSetup B;
                 TRY(batch_prepare(ts.data(), shots, nshot, si, dt, nt, b0, b1, Kh, geo, S, B));
                 const int trial = std::min(nt, 12);
-                for (int n = 0; n < 2; ++n) launch_batch_any(H, si, B.d_args, B.d_tile0, nshot, n, B.nblk, s);
+                for (int n = 0; n < 2; ++n) launch_batch_any(H, si, B.d_args, B.d_tile0, B.d_shot_of, nshot, n, B.nblk, s);
                 IB_CUDA(cudaEventRecord(e0, s));
-                for (int n = 0; n < trial; ++n) launch_batch_any(H, si, B.d_args, B.d_tile0, nshot, n, B.nblk, s);
+                for (int n = 0; n < trial; ++n) launch_batch_any(H, si, B.d_args, B.d_tile0, B.d_shot_of, nshot, n, B.nblk, s);
                 IB_CUDA(cudaEventRecord(e1, s));
                 IB_CUDA(cudaEventSynchronize(e1));
                 float ms = 0.f;
@@ -2056,10 +2082,10 @@ extern "C" ib_status ib_forward_batch(const ib_table* const* tables, const ib_sh
     for (int n = 0; n < nt; ++n) {
         StepArgs<float>* dargs = B.d_args;
         switch (H) {
-            case 1: launch_batch_shape<1>(best, dargs, B.d_tile0, nshot, n, B.nblk, cs); break;
-            case 2: launch_batch_shape<2>(best, dargs, B.d_tile0, nshot, n, B.nblk, cs); break;
-            case 3: launch_batch_shape<3>(best, dargs, B.d_tile0, nshot, n, B.nblk, cs); break;
-            default: launch_batch_shape<4>(best, dargs, B.d_tile0, nshot, n, B.nblk, cs); break;
+            case 1: launch_batch_shape<1>(best, dargs, B.d_tile0, B.d_shot_of, nshot, n, B.nblk, cs); break;
+            case 2: launch_batch_shape<2>(best, dargs, B.d_tile0, B.d_shot_of, nshot, n, B.nblk, cs); break;
+            case 3: launch_batch_shape<3>(best, dargs, B.d_tile0, B.d_shot_of, nshot, n, B.nblk, cs); break;
+            default: launch_batch_shape<4>(best, dargs, B.d_tile0, B.d_shot_of, nshot, n, B.nblk, cs); break;
         }
     }
     cudaError_t ce = cudaStreamEndCapture(cs, &graph);
