@@ -891,23 +891,57 @@ struct AdjArgs {
 
 template <typename T, int H, int TX, int TZ>
 __global__ void __launch_bounds__(256) k_adj2d(AdjArgs<T> a) {
-    __shared__ T tile[TZ + 2 * H][TX + 2 * H];
+    static_assert((TZ * TX) % 256 == 0, "whole points per thread");
+    constexpr int PT = TZ * TX / 256, NT = (TZ + 2 * H) * (TX + 2 * H);
+    __shared__ T tile[TZ + 2 * H][TX + 2 * H];     // K mu on the halo tile
+    __shared__ T tmu[NT];
     __shared__ T acc[TZ * TX];
     __shared__ T sw[TZ * TX];     // source weights landing in the tile
     const int tid = threadIdx.x;
     const int64_t x0 = (int64_t)blockIdx.x * TX, z0 = (int64_t)blockIdx.y * TZ;
     const Layout& L = a.L;
-    for (int i = tid; i < TZ * TX; i += 256) sw[i] = (T)0;
-    for (int i = tid; i < (TZ + 2 * H) * (TX + 2 * H); i += 256) {
-        int lz = i / (TX + 2 * H), lx = i - lz * (TX + 2 * H);
-        int64_t x = x0 + lx - H, z = z0 + lz - H;
-        T v = 0;
-        if (x < L.nx + H && z < L.nz + H) {
-            int64_t q = L.base + z * L.px + x;
-            v = a.Kh[q] * a.mu[q];
-        }
-        tile[lz][lx] = v;
+    const int64_t origin = L.base + z0 * L.px + x0;
+    const int64_t tile_id = (int64_t)blockIdx.y * a.opT.ntx + blockIdx.x;
+    // K and mu halo tiles arrive by cp.async ...
+    for (int i = tid; i < NT; i += 256) {
+        const int lz = i / (TX + 2 * H), lx = i - lz * (TX + 2 * H);
+        const int64_t x = x0 + lx - H, z = z0 + lz - H;
+        const bool ok = x < L.nx + H && z < L.nz + H;
+        const int64_t q = ok ? L.base + z * L.px + x : 0;
+        cp_async<(int)sizeof(T)>(&tile[lz][lx], a.Kh + q, ok);
+        cp_async<(int)sizeof(T)>(&tmu[i], a.mu + q, ok);
     }
+    cp_async_commit();
+    for (int i = tid; i < TZ * TX; i += 256) sw[i] = (T)0;
+    // ... while this thread's operands and the tile's entry ranges load
+    T mu_v[PT], mum_v[PT], kh_v[PT], p0_v[PT], p1_v[PT], p2_v[PT], g_v[PT];
+    bool msk[PT];
+#pragma unroll
+    for (int j = 0; j < PT; ++j) {
+        const int i = tid + 256 * j, lz = i / TX, lx = i - lz * TX;
+        const bool in = x0 + lx < L.nx && z0 + lz < L.nz;
+        const int64_t q = origin + lz * L.px + lx;
+        mu_v[j] = in ? a.mu[q] : (T)0;
+        mum_v[j] = in ? a.mum[q] : (T)0;
+        kh_v[j] = in ? a.Kh[q] : (T)0;
+        msk[j] = in ? a.mask[q] != 0 : false;
+        p0_v[j] = in ? a.pm0[q] : (T)0;
+        p1_v[j] = in ? a.pm1[q] : (T)0;
+        p2_v[j] = in ? a.pm2[q] : (T)0;
+        g_v[j] = in ? a.grad[q] : (T)0;
+    }
+    int32_t e0 = 0, e1 = 0, j0 = 0, j1 = 0;
+    if (a.opT.ptr) {
+        e0 = a.opT.ptr[tile_id];
+        e1 = a.opT.ptr[tile_id + 1];
+    }
+    if (a.inj.tile_ptr) {
+        j0 = a.inj.tile_ptr[tile_id];
+        j1 = a.inj.tile_ptr[tile_id + 1];
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    for (int i = tid; i < NT; i += 256) (&tile[0][0])[i] *= tmu[i];
     __syncthreads();
     for (int i = tid; i < TZ * TX; i += 256) {
         int lz = i / TX, lx = i - lz * TX;
@@ -919,28 +953,22 @@ __global__ void __launch_bounds__(256) k_adj2d(AdjArgs<T> a) {
                             ((tile[lz + H + k][lx + H] - c) + (tile[lz + H - k][lx + H] - c)));
         acc[i] = s;
     }
-    tile_sources<T, TX, TZ>(a.src, (T)1, L.base + z0 * L.px + x0, L.px, sw, tid);
+    tile_sources<T, TX, TZ>(a.src, (T)1, origin, L.px, sw, tid);
     __syncthreads();
-    const int64_t tile_id = (int64_t)blockIdx.y * a.opT.ntx + blockIdx.x;
-    const int64_t origin = L.base + z0 * L.px + x0;
-    if (a.opT.ptr) {
-        const int32_t e0 = a.opT.ptr[tile_id], e1 = a.opT.ptr[tile_id + 1];
-        for (int32_t e = e0 + tid; e < e1; e += 256) {
-            int64_t s = origin + a.opT.src[e];
-            atomicAdd(&acc[a.opT.loc[e]], a.opT.w[e] * (a.Kh[s] * a.mu[s]));
-        }
+    for (int32_t e = e0 + tid; e < e1; e += 256) {
+        int64_t s = origin + a.opT.src[e];
+        atomicAdd(&acc[a.opT.loc[e]], a.opT.w[e] * (a.Kh[s] * a.mu[s]));
     }
     __syncthreads();
-    for (int i = tid; i < TZ * TX; i += 256) {
-        int lz = i / TX, lx = i - lz * TX;
-        int64_t x = x0 + lx, z = z0 + lz;
-        if (x >= L.nx || z >= L.nz) continue;
-        acc[i] = a.mask[origin + lz * L.px + lx] ? acc[i] : (T)0;
+#pragma unroll
+    for (int j = 0; j < PT; ++j) {
+        const int i = tid + 256 * j;
+        if (!msk[j]) acc[i] = (T)0;
     }
     __syncthreads();
-    if (a.inj.tile_ptr) {
+    if (j1 > j0) {
         const int warp = tid >> 5, lane = tid & 31;
-        for (int k = a.inj.tile_ptr[tile_id] + warp; k < a.inj.tile_ptr[tile_id + 1]; k += 8) {
+        for (int k = j0 + warp; k < j1; k += 8) {
             const int32_t r = a.inj.perm[k];
             const int64_t q = a.inj.row_pad[r];
             T s = 0;
@@ -957,19 +985,19 @@ __global__ void __launch_bounds__(256) k_adj2d(AdjArgs<T> a) {
     }
     __syncthreads();
     const T wv = a.src.n ? a.wavelet[a.m - 1] : (T)0;
-    for (int i = tid; i < TZ * TX; i += 256) {
-        int lz = i / TX, lx = i - lz * TX;
-        int64_t x = x0 + lx, z = z0 + lz;
-        if (x >= L.nx || z >= L.nz) continue;
-        int64_t q = origin + lz * L.px + lx;
-        T mu_new = (T)2 * a.mu[q] - a.mum[q] + acc[i];
+#pragma unroll
+    for (int j = 0; j < PT; ++j) {
+        const int i = tid + 256 * j, lz = i / TX, lx = i - lz * TX;
+        if (x0 + lx >= L.nx || z0 + lz >= L.nz) continue;
+        const int64_t q = origin + lz * L.px + lx;
+        const T mu_new = (T)2 * mu_v[j] - mum_v[j] + acc[i];
         a.out[q] = mu_new;
-        T Kq = a.Kh[q];
+        const T Kq = kh_v[j];
         if (Kq > (T)0) {
-            T d2 = (a.pm0[q] - a.pm1[q]) - (a.pm1[q] - a.pm2[q]);
+            T d2 = (p0_v[j] - p1_v[j]) - (p1_v[j] - p2_v[j]);
             const T srcw = sw[i];
             d2 -= srcw * wv;
-            a.grad[q] += mu_new * (a.two_dt_over_h / sqrt(Kq)) * d2;
+            a.grad[q] = g_v[j] + mu_new * (a.two_dt_over_h / sqrt(Kq)) * d2;
             if (a.gw && srcw != (T)0) atomicAdd(&a.gw[a.m - 1], srcw * mu_new);
         }
     }
