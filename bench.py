@@ -609,8 +609,10 @@ def run_shots(args, world, rank, local, dev, dist):
     2000 steps) in one batched, graph-captured launch per step; one step = the
     forward of all shots (tables built once, reported as setup).  The same shots
     one launch per shot and step are timed once for comparison.
-    adjoint2d: the same shots one after the other, forward with 40 checkpoints +
-    adjoint (velocity gradient of the L2 misfit); one step = all shots."""
+    adjoint2d: the same shots, batched forward with 40 checkpoints + batched
+    adjoint (velocity gradient of the L2 misfit, the whole backward pass one
+    captured graph); one step = all shots.  The same shots one ib_forward +
+    ib_adjoint call per shot are timed once for comparison."""
     import torch
     from paper_2309_03600_gb300 import ib, inputs
     nt = args.nt or 2000
@@ -639,14 +641,19 @@ def run_shots(args, world, rank, local, dev, dist):
         for t in tables:
             ckpts.append(torch.empty(ib.ib_checkpoint_bytes(t, 32, nt, n_ckpt), dtype=torch.uint8, device=dev))
 
+    def per_shot_adjoint():
+        for t, sh, ck in zip(tables, shots, ckpts):
+            tr = ib.ib_forward(t, sh["vel"], sh["wavelet"], sh["src"], sh["rec"], dt, nt, ckpt=ck,
+                               n_ckpt=n_ckpt)
+            ib.ib_adjoint(t, sh["vel"], sh["wavelet"], sh["src"], sh["rec"], dt, nt, ck, n_ckpt, tr)
+
     def step():
         if args.workload == "batch2d":
             ib.ib_forward_batch(tables, shots, dt, nt)
         else:
-            for t, sh, ck in zip(tables, shots, ckpts):
-                tr = ib.ib_forward(t, sh["vel"], sh["wavelet"], sh["src"], sh["rec"], dt, nt, ckpt=ck,
-                                   n_ckpt=n_ckpt)
-                ib.ib_adjoint(t, sh["vel"], sh["wavelet"], sh["src"], sh["rec"], dt, nt, ck, n_ckpt, tr)
+            # residual = traces (observed data zero): the misfit gradient of all shots
+            outs = ib.ib_forward_batch_ckpt(tables, shots, dt, nt, ckpts, n_ckpt)
+            ib.ib_adjoint_batch(tables, shots, dt, nt, ckpts, n_ckpt, outs)
 
     for _ in range(args.warmup):
         flush.zero_()
@@ -703,16 +710,29 @@ def run_shots(args, world, rank, local, dev, dist):
         compare = {"one_shot_per_launch_value": N * nt / (ms1 * 1e-3), "one_shot_per_launch_ms": ms1,
                    "batched_speedup": ms1 / ms}
     else:
-        a = prof.get("adj2d_f32")
+        a = prof.get("adj2d_batch_graph_f32")
         if a and a["sampled"]:
             avg = a["sampled_ms"] / a["sampled"] * 1e-3
-            # adjoint kernel: mu, mu_prev, Kh, mask, three stored p, grad RMW, mu_next per point
-            avg_N = N / len(shots)
-            byts = (4 * 7 + 1 + 4) * avg_N
+            # one replay = the backward pass of all shots: per step and point the adjoint
+            # kernel moves 33 B (mu, mu_prev, K, mask, three stored p, gradient
+            # read + write, mu_next) and the recompute 16 B; plus the segment restores
+            byts = nt * N * (33 + 16) + n_ckpt * 4 * N * 4
             ach = byts / avg / 1e9
-            roof = {"bound": "hbm", "kernel": "adj2d_f32", "achieved": ach, "peak": peak, "peak_kind": peak_kind,
-                    "unit": "GB/s", "frac": ach / peak, "traffic": None, "algorithmic_bytes_per_launch": byts,
-                    "avg_launch_us": avg * 1e6, "frac_of_nominal_8TBs": ach / 8000.0}
+            roof = {"bound": "hbm", "kernel": "adj2d_batch_graph_f32", "achieved": ach, "peak": peak,
+                    "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / peak, "traffic": None,
+                    "algorithmic_bytes_per_launch": byts, "avg_launch_us": avg * 1e6,
+                    "frac_of_nominal_8TBs": ach / 8000.0, "note": "correction-table bytes not counted"}
+        flush.zero_()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        per_shot_adjoint()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms1 = e0.elapsed_time(e1)
+        compare = {"per_shot_calls_value": N * nt / (ms1 * 1e-3), "per_shot_calls_ms": ms1,
+                   "batched_speedup": ms1 / ms}
     if rank != 0:
         return 0
     out = {
@@ -721,7 +741,7 @@ def run_shots(args, world, rank, local, dev, dist):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": args.workload, "shots": len(shots), "points": N, "nt": nt, "space_order": 8,
                    "step": ("batched forward of all shots (tables prebuilt)" if args.workload == "batch2d"
-                            else "forward with 40 checkpoints + adjoint gradient, all shots"),
+                            else "batched forward with 40 checkpoints + batched adjoint gradient, all shots"),
                    "l2": "flushed between steps (256 MB write)"},
         "setup": {"seconds": t_setup, "ib_rows": sum(t.stats()["rows"][0] for t in tables)},
         "roofline": roof, "kernels": kernels, "compare": compare, "e2e": None, "cpu_baseline": None,

@@ -208,6 +208,34 @@ ib_status ib_forward_batch(const ib_table* const* tables, const ib_shot* shots,
                            void* stream);
 
 /*
+ * ib_forward_batch_ckpt -- ib_forward_batch that also fills each shot's
+ * checkpoint buffer ckpts[i] (device, ib_checkpoint_bytes(tables[i], 32, nt,
+ * n_ckpt) bytes, the layout ib_forward writes), so that either ib_adjoint per
+ * shot or ib_adjoint_batch can follow.  ckpts is a host array of nshot device
+ * pointers.  Errors: those of ib_forward_batch; IB_ERR_ARG for a null array
+ * or buffer or n_ckpt < 1.
+ */
+ib_status ib_forward_batch_ckpt(const ib_table* const* tables, const ib_shot* shots,
+                                int32_t nshot, int32_t precision, double dt, int32_t nt,
+                                void* const* ckpts, int32_t n_ckpt, void* stream);
+
+/*
+ * ib_adjoint_batch -- ib_adjoint (same transpose, same checkpoint segments)
+ * for many shots at once: every recompute step and every adjoint step is one
+ * launch over the tiles of all shots, and the whole backward pass is one
+ * captured graph.  Per shot i: checkpoints ckpts[i] from ib_forward_batch_ckpt
+ * or ib_forward with the same dt, nt and n_ckpt; residuals[i] [nrec][nt];
+ * grads[i] [N] receives dJ/dc (overwritten).  Host arrays of nshot device
+ * pointers; FP32, 2D second-order tables sharing the space order; no wavelet
+ * gradient.  Errors: IB_ERR_ARG (null or mismatched inputs), IB_ERR_STATE
+ * (other forms), IB_ERR_OOM, IB_ERR_CUDA.
+ */
+ib_status ib_adjoint_batch(const ib_table* const* tables, const ib_shot* shots,
+                           int32_t nshot, int32_t precision, double dt, int32_t nt,
+                           const void* const* ckpts, int32_t n_ckpt,
+                           const void* const* residuals, void* const* grads, void* stream);
+
+/*
  * ib_forward_noalloc -- ib_forward for callers that cannot allocate device
  * memory (the paper has no counterpart; this is a deployment variant).  Some
  * callers own every device allocation themselves -- a host framework with its

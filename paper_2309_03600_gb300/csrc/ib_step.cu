@@ -296,6 +296,61 @@ __global__ void __launch_bounds__(256) k_leap2d_batch(const StepArgs<T>* __restr
     leap2d_tile<T, H, TX, TZ>(a, local % a.ntx, local / a.ntx, tile, acc, sadd);
 }
 
+// Batched recompute step n of a checkpoint segment: the shot's segment buffer
+// (buf0) holds p^{c-1+j} in slot j, and step n = c + j writes slot j + 2.
+template <typename T, int H, int TX, int TZ>
+__global__ void __launch_bounds__(256) k_leap2d_batch_seg(const StepArgs<T>* __restrict__ shots,
+                                                          const int64_t* __restrict__ tile0,
+                                                          const int32_t* __restrict__ shot_of, int n, int j) {
+    __shared__ T tile[TZ + 2 * H][TX + 2 * H];
+    __shared__ T acc[TZ * TX];
+    __shared__ T sadd[TZ * TX];
+    const int64_t b = blockIdx.x;
+    const int sh = shot_of[b];
+    StepArgs<T> a = shots[sh];
+    const int64_t local = b - tile0[sh];
+    if (local >= a.ntiles) return;   // uniform per block
+    const int64_t tot = a.L.total;
+    a.p = a.buf0 + (int64_t)(j + 1) * tot;
+    a.pm = a.buf0 + (int64_t)j * tot;
+    a.out = a.buf0 + (int64_t)(j + 2) * tot;
+    a.step = n;
+    leap2d_tile<T, H, TX, TZ>(a, local % a.ntx, local / a.ntx, tile, acc, sadd);
+}
+
+// Per-shot field copies between wavefield buffers, checkpoints and segment buffers
+template <typename T>
+struct ShotCopy {
+    const T* a;           // batched forward: the shot's buf0 (steps n even: p^n) ...
+    const T* b;           // ... and buf1; adjoint restore: the checkpoint slot base
+    T* dst;               // checkpoint base (forward) or segment buffer (restore)
+    int64_t total;        // padded field size
+};
+
+// forward, before step n: checkpoint k = [p^n, p^{n-1}] of every shot
+template <typename T>
+__global__ void k_ckpt_batch(const ShotCopy<T>* __restrict__ items, int n, int k) {
+    const ShotCopy<T> it = items[blockIdx.y];
+    const T* cur = (n & 1) ? it.b : it.a;
+    const T* prev = (n & 1) ? it.a : it.b;
+    T* slot = it.dst + (int64_t)k * 2 * it.total;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < it.total; i += (int64_t)gridDim.x * blockDim.x) {
+        slot[i] = cur[i];
+        slot[it.total + i] = prev[i];
+    }
+}
+
+// adjoint, start of segment k: segment slots 0, 1 = p^{c-1}, p^c from checkpoint k
+template <typename T>
+__global__ void k_seg_restore_batch(const ShotCopy<T>* __restrict__ items, int k) {
+    const ShotCopy<T> it = items[blockIdx.y];
+    const T* slot = it.a + (int64_t)k * 2 * it.total;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < it.total; i += (int64_t)gridDim.x * blockDim.x) {
+        it.dst[i] = slot[it.total + i];
+        it.dst[it.total + i] = slot[i];
+    }
+}
+
 // receivers only (after the last step)
 template <typename T>
 __global__ void k_receivers(PointSet<T> rec, const T* p, T* traces, int nt, int col) {
@@ -889,19 +944,17 @@ struct AdjArgs {
     T* gw;               // [nt] or null
 };
 
+// one adjoint tile (bx, bz); shared arrays from the calling kernel
 template <typename T, int H, int TX, int TZ>
-__global__ void __launch_bounds__(256) k_adj2d(AdjArgs<T> a) {
+__device__ __forceinline__ void adj2d_tile(const AdjArgs<T>& a, int64_t bx, int64_t bz, T (*tile)[TX + 2 * H], T* tmu,
+                                           T* acc, T* sw) {
     static_assert((TZ * TX) % 256 == 0, "whole points per thread");
     constexpr int PT = TZ * TX / 256, NT = (TZ + 2 * H) * (TX + 2 * H);
-    __shared__ T tile[TZ + 2 * H][TX + 2 * H];     // K mu on the halo tile
-    __shared__ T tmu[NT];
-    __shared__ T acc[TZ * TX];
-    __shared__ T sw[TZ * TX];     // source weights landing in the tile
     const int tid = threadIdx.x;
-    const int64_t x0 = (int64_t)blockIdx.x * TX, z0 = (int64_t)blockIdx.y * TZ;
+    const int64_t x0 = bx * TX, z0 = bz * TZ;
     const Layout& L = a.L;
     const int64_t origin = L.base + z0 * L.px + x0;
-    const int64_t tile_id = (int64_t)blockIdx.y * a.opT.ntx + blockIdx.x;
+    const int64_t tile_id = bz * a.opT.ntx + bx;
     // K and mu halo tiles arrive by cp.async ...
     for (int i = tid; i < NT; i += 256) {
         const int lz = i / (TX + 2 * H), lx = i - lz * (TX + 2 * H);
@@ -1001,6 +1054,53 @@ __global__ void __launch_bounds__(256) k_adj2d(AdjArgs<T> a) {
             if (a.gw && srcw != (T)0) atomicAdd(&a.gw[a.m - 1], srcw * mu_new);
         }
     }
+}
+
+template <typename T, int H, int TX, int TZ>
+__global__ void __launch_bounds__(256) k_adj2d(AdjArgs<T> a) {
+    __shared__ T tile[TZ + 2 * H][TX + 2 * H];     // K mu on the halo tile
+    __shared__ T tmu[(TZ + 2 * H) * (TX + 2 * H)];
+    __shared__ T acc[TZ * TX];
+    __shared__ T sw[TZ * TX];                      // source weights landing in the tile
+    adj2d_tile<T, H, TX, TZ>(a, blockIdx.x, blockIdx.y, tile, tmu, acc, sw);
+}
+
+// Batched adjoint step m of segment [c, e) over many shots: block -> (shot, tile)
+// by table.  mu^{m+1} / mu^{m+2} alternate between the shot's two buffers with
+// the number of steps taken (nt - m); the segment buffer holds p^{c-1+j} in slot j.
+template <typename T>
+struct AdjBatch {
+    AdjArgs<T> a;
+    T* mu1;
+    T* mu2;
+    T* seg;               // segment buffer: (seg_len + 2) padded fields
+};
+
+template <typename T, int H, int TX, int TZ>
+__global__ void __launch_bounds__(256) k_adj2d_batch(const AdjBatch<T>* __restrict__ shots,
+                                                     const int64_t* __restrict__ tile0,
+                                                     const int32_t* __restrict__ shot_of, int m, int j, int nt) {
+    __shared__ T tile[TZ + 2 * H][TX + 2 * H];
+    __shared__ T tmu[(TZ + 2 * H) * (TX + 2 * H)];
+    __shared__ T acc[TZ * TX];
+    __shared__ T sw[TZ * TX];
+    const int64_t b = blockIdx.x;
+    const int sh = shot_of[b];
+    const AdjBatch<T>& B = shots[sh];
+    AdjArgs<T> a = B.a;
+    const bool even = ((nt - m) & 1) == 0;
+    a.mu = even ? B.mu1 : B.mu2;
+    a.mum = even ? B.mu2 : B.mu1;
+    a.out = const_cast<T*>(a.mum);
+    a.m = m;
+    const int64_t tot = a.L.total;
+    a.pm0 = B.seg + (int64_t)(j + 1) * tot;
+    a.pm1 = B.seg + (int64_t)j * tot;
+    a.pm2 = B.seg + (int64_t)(j - 1) * tot;
+    const int64_t local = b - tile0[sh];
+    const int64_t ntiles = a.opT.ntx * ((a.L.nz + TZ - 1) / TZ);
+    if (local >= ntiles) return;   // uniform per block
+    adj2d_tile<T, H, TX, TZ>(a, local % a.opT.ntx, local / a.opT.ntx, tile, tmu, acc, sw);
 }
 
 // ---------------------------------------------------------------------------
@@ -2006,9 +2106,14 @@ static ib_status batch_prepare(ib_table* const* ts, const ib_shot* shots, int ns
     return IB_OK;
 }
 
-extern "C" ib_status ib_forward_batch(const ib_table* const* tables, const ib_shot* shots, int32_t nshot,
-                                      int32_t precision, double dt, int32_t nt, void* stream) {
+static ib_status forward_batch_impl(const ib_table* const* tables, const ib_shot* shots, int32_t nshot,
+                                    int32_t precision, double dt, int32_t nt, void* const* ckpts, int32_t n_ckpt,
+                                    void* stream) {
     ib_set_error("");
+    if (ckpts && n_ckpt < 1) {
+        ib_set_error("n_ckpt must be >= 1");
+        return IB_ERR_ARG;
+    }
     if (!tables || !shots || nshot < 1) {
         ib_set_error("empty batch");
         return IB_ERR_ARG;
@@ -2097,6 +2202,25 @@ extern "C" ib_status ib_forward_batch(const ib_table* const* tables, const ib_sh
     }
     BatchSetup B;
     TRY(batch_prepare(ts.data(), shots, nshot, best, dt, nt, b0, b1, Kh, geo, S, B));
+    // checkpoint copies (ib_forward's layout: slot k = [p^{k seg}, p^{k seg - 1}])
+    ShotCopy<float>* d_items = nullptr;
+    int64_t seg = 0, maxtot = 0;
+    if (ckpts) {
+        std::vector<ShotCopy<float>> items(nshot);
+        for (int i = 0; i < nshot; ++i) {
+            if (!ckpts[i]) {
+                ib_set_error("null checkpoint buffer");
+                return IB_ERR_ARG;
+            }
+            items[i] = {b0[i], b1[i], (float*)ckpts[i], ts[i]->L.total};
+            maxtot = std::max(maxtot, ts[i]->L.total);
+        }
+        TRY(S.alloc(&d_items, nshot));
+        IB_CUDA(cudaMemcpyAsync(d_items, items.data(), sizeof(ShotCopy<float>) * nshot, cudaMemcpyHostToDevice, s));
+        IB_CUDA(cudaStreamSynchronize(s));
+        seg = ckpt_seg(nt, n_ckpt);
+    }
+    const dim3 cgrid((unsigned)std::min<int64_t>((maxtot + 255) / 256, 256), (unsigned)nshot);
     // ---- all nt steps as one captured graph
     cudaStream_t cs;
     IB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
@@ -2108,6 +2232,7 @@ extern "C" ib_status ib_forward_batch(const ib_table* const* tables, const ib_sh
     cudaGraphExec_t exec = nullptr;
     IB_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
     for (int n = 0; n < nt; ++n) {
+        if (d_items && n % seg == 0) k_ckpt_batch<float><<<cgrid, 256, 0, cs>>>(d_items, n, (int)(n / seg));
         StepArgs<float>* dargs = B.d_args;
         switch (H) {
             case 1: launch_batch_shape<1>(best, dargs, B.d_tile0, B.d_shot_of, nshot, n, B.nblk, cs); break;
@@ -2141,6 +2266,216 @@ extern "C" ib_status ib_forward_batch(const ib_table* const* tables, const ib_sh
     cudaGraphDestroy(graph);
     cudaEventDestroy(ready);
     cudaStreamDestroy(cs);
+    return IB_OK;
+}
+
+extern "C" ib_status ib_forward_batch(const ib_table* const* tables, const ib_shot* shots, int32_t nshot,
+                                      int32_t precision, double dt, int32_t nt, void* stream) {
+    return forward_batch_impl(tables, shots, nshot, precision, dt, nt, nullptr, 0, stream);
+}
+
+extern "C" ib_status ib_forward_batch_ckpt(const ib_table* const* tables, const ib_shot* shots, int32_t nshot,
+                                           int32_t precision, double dt, int32_t nt, void* const* ckpts,
+                                           int32_t n_ckpt, void* stream) {
+    if (!ckpts) {
+        ib_set_error("null checkpoint array");
+        return IB_ERR_ARG;
+    }
+    return forward_batch_impl(tables, shots, nshot, precision, dt, nt, ckpts, n_ckpt, stream);
+}
+
+// ---------------------------------------------------------------------------
+// batched adjoint: every shot's segments in lockstep, one graph for the whole
+// backward pass (segment restore, batched recompute steps, batched adjoint steps)
+// ---------------------------------------------------------------------------
+template <int H>
+static void launch_adj_batch_h(const StepArgs<float>* fargs, const AdjBatch<float>* aargs, const ShotCopy<float>* rst,
+                               const int64_t* tile0, const int32_t* shot_of, int64_t nblk, dim3 cgrid, int nt,
+                               int64_t c, int64_t e, int k, cudaStream_t s) {
+    k_seg_restore_batch<float><<<cgrid, 256, 0, s>>>(rst, k);
+    for (int64_t n = c; n < e; ++n)
+        k_leap2d_batch_seg<float, H, 64, 8><<<(unsigned)nblk, 256, 0, s>>>(fargs, tile0, shot_of, (int)n, (int)(n - c));
+    for (int64_t m = e; m >= c + 1; --m)
+        k_adj2d_batch<float, H, 64, 8><<<(unsigned)nblk, 256, 0, s>>>(aargs, tile0, shot_of, (int)m, (int)(m - c), nt);
+}
+
+extern "C" ib_status ib_adjoint_batch(const ib_table* const* tables, const ib_shot* shots, int32_t nshot,
+                                      int32_t precision, double dt, int32_t nt, const void* const* ckpts,
+                                      int32_t n_ckpt, const void* const* residuals, void* const* grads,
+                                      void* stream) {
+    ib_set_error("");
+    if (!tables || !shots || nshot < 1 || !ckpts || !residuals || !grads || n_ckpt < 1) {
+        ib_set_error("batched adjoint needs tables, shots, checkpoints, residuals and gradients");
+        return IB_ERR_ARG;
+    }
+    if (precision != 32) {
+        ib_set_error("batched shots run in FP32");
+        return IB_ERR_ARG;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    std::vector<ib_table*> ts(nshot);
+    int H = -1;
+    for (int i = 0; i < nshot; ++i) {
+        TRY(check_shot(tables[i], &shots[i], precision, dt, nt, false));
+        ts[i] = const_cast<ib_table*>(tables[i]);
+        if (ts[i]->form != IB_SECOND_ORDER || ts[i]->grid.ndim != 2) {
+            ib_set_error("batched adjoint: 2D second-order tables only");
+            return IB_ERR_STATE;
+        }
+        if (!ckpts[i] || !residuals[i] || !grads[i]) {
+            ib_set_error("null checkpoint, residual or gradient buffer");
+            return IB_ERR_ARG;
+        }
+        const int h = ts[i]->opts.space_order / 2;
+        if (H >= 0 && h != H) {
+            ib_set_error("batched shots must share the space order");
+            return IB_ERR_ARG;
+        }
+        H = h;
+    }
+    const int64_t seg = ckpt_seg(nt, n_ckpt);
+    Scratch S(s);
+    std::vector<StepArgs<float>> fargs(nshot);
+    std::vector<AdjBatch<float>> aargs(nshot);
+    std::vector<ShotCopy<float>> rst(nshot);
+    std::vector<float*> grad(nshot);
+    std::vector<int64_t> tile0(nshot + 1, 0);
+    std::vector<TileBins> keep;
+    int64_t maxtot = 0;
+    for (int i = 0; i < nshot; ++i) {
+        ib_table* t = ts[i];
+        const Layout& L = t->L;
+        float *Kh, *mu1, *mu2, *segbuf;
+        TRY(S.alloc(&Kh, L.total, true));
+        TRY(S.alloc(&mu1, L.total, true));
+        TRY(S.alloc(&mu2, L.total, true));
+        TRY(S.alloc(&grad[i], L.total, true));
+        TRY(S.alloc(&segbuf, (seg + 2) * L.total, true));
+        k_leap_coef<float><<<grid1(L.N, 256), 256, 0, s>>>(L, (const float*)shots[i].vel_dev, t->mask_pad[0],
+                                                           dt / t->grid.h, Kh);
+        IB_CHECK_LAUNCH("k_leap_coef");
+        ib_count_launch("setup");
+        Geom<float> g;
+        TRY(setup_points<float>(t, &shots[i], dt * dt / pow(t->grid.h, 2), S, g));
+        const TileBins* fb = nullptr;
+        const TileBins* tb = nullptr;
+        TRY(ib_table_bins(t, 0, false, TX2, 1, TZ2, &fb, s));
+        TRY(ib_table_bins(t, 0, true, TX2, 1, TZ2, &tb, s));
+        RowView<float> inj;
+        TRY(build_injection<float>(L, g.rec, S, inj, keep));
+        StepArgs<float>& fa = fargs[i];
+        memset(&fa, 0, sizeof fa);
+        fa.L = L;
+        float c1u[4];
+        stencil_weights<float>(t->opts.space_order, fa.w2, c1u);
+        fa.Kh = Kh;
+        fa.op = tview<float>(fb);
+        fa.src = g.src;
+        fa.wavelet = (const float*)shots[i].wavelet_dev;
+        fa.rec.n = 0;
+        fa.rec_step = -1;
+        fa.nt = nt;
+        fa.buf0 = segbuf;
+        fa.ntx = (L.nx + TX2 - 1) / TX2;
+        fa.ntiles = fa.ntx * ((L.nz + TZ2 - 1) / TZ2);
+        AdjArgs<float>& aa = aargs[i].a;
+        memset(&aa, 0, sizeof aa);
+        aa.L = L;
+        for (int k = 0; k < 5; ++k) aa.w2[k] = fa.w2[k];
+        aa.Kh = Kh;
+        aa.mask = t->mask_pad[0];
+        aa.two_dt_over_h = (float)(2.0 * dt / t->grid.h);
+        aa.opT = tview<float>(tb);
+        aa.opT.ntx = fa.ntx;
+        aa.inj = inj;
+        aa.inj.ntx = fa.ntx;
+        aa.res = (const float*)residuals[i];
+        aa.nt = nt;
+        aa.grad = grad[i];
+        aa.src = g.src;
+        aa.wavelet = (const float*)shots[i].wavelet_dev;
+        aa.gw = nullptr;
+        aargs[i].mu1 = mu1;
+        aargs[i].mu2 = mu2;
+        aargs[i].seg = segbuf;
+        rst[i] = {(const float*)ckpts[i], nullptr, segbuf, L.total};
+        tile0[i + 1] = tile0[i] + fa.ntiles;
+        maxtot = std::max(maxtot, L.total);
+    }
+    const int64_t nblk = tile0[nshot];
+    std::vector<int32_t> shot_of(nblk);
+    for (int i = 0; i < nshot; ++i)
+        for (int64_t b = tile0[i]; b < tile0[i + 1]; ++b) shot_of[b] = i;
+    StepArgs<float>* d_f;
+    AdjBatch<float>* d_a;
+    ShotCopy<float>* d_r;
+    int64_t* d_t0;
+    int32_t* d_so;
+    TRY(S.alloc(&d_f, nshot));
+    TRY(S.alloc(&d_a, nshot));
+    TRY(S.alloc(&d_r, nshot));
+    TRY(S.alloc(&d_t0, nshot + 1));
+    TRY(S.alloc(&d_so, std::max<int64_t>(nblk, 1)));
+    IB_CUDA(cudaMemcpyAsync(d_f, fargs.data(), sizeof(StepArgs<float>) * nshot, cudaMemcpyHostToDevice, s));
+    IB_CUDA(cudaMemcpyAsync(d_a, aargs.data(), sizeof(AdjBatch<float>) * nshot, cudaMemcpyHostToDevice, s));
+    IB_CUDA(cudaMemcpyAsync(d_r, rst.data(), sizeof(ShotCopy<float>) * nshot, cudaMemcpyHostToDevice, s));
+    IB_CUDA(cudaMemcpyAsync(d_t0, tile0.data(), 8 * (nshot + 1), cudaMemcpyHostToDevice, s));
+    IB_CUDA(cudaMemcpyAsync(d_so, shot_of.data(), 4 * nblk, cudaMemcpyHostToDevice, s));
+    IB_CUDA(cudaStreamSynchronize(s));   // the host tables go out of scope
+    const dim3 cgrid((unsigned)std::min<int64_t>((maxtot + 255) / 256, 256), (unsigned)nshot);
+    // ---- the whole backward pass as one captured graph
+    cudaStream_t cs;
+    IB_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+    cudaEvent_t ready;
+    IB_CUDA(cudaEventCreateWithFlags(&ready, cudaEventDisableTiming));
+    IB_CUDA(cudaEventRecord(ready, s));
+    IB_CUDA(cudaStreamWaitEvent(cs, ready, 0));
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    IB_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    int64_t nadj = 0;
+    for (int k = n_ckpt - 1; k >= 0; --k) {
+        const int64_t c = (int64_t)k * seg;
+        if (c >= nt) continue;
+        const int64_t e = std::min<int64_t>(c + seg, nt);
+        switch (H) {
+            case 1: launch_adj_batch_h<1>(d_f, d_a, d_r, d_t0, d_so, nblk, cgrid, nt, c, e, k, cs); break;
+            case 2: launch_adj_batch_h<2>(d_f, d_a, d_r, d_t0, d_so, nblk, cgrid, nt, c, e, k, cs); break;
+            case 3: launch_adj_batch_h<3>(d_f, d_a, d_r, d_t0, d_so, nblk, cgrid, nt, c, e, k, cs); break;
+            default: launch_adj_batch_h<4>(d_f, d_a, d_r, d_t0, d_so, nblk, cgrid, nt, c, e, k, cs); break;
+        }
+        nadj += e - c;
+    }
+    cudaError_t ce = cudaStreamEndCapture(cs, &graph);
+    if (ce != cudaSuccess) return ib_cuda_fail(ce, "graph capture", __FILE__, __LINE__);
+    ce = cudaGraphInstantiate(&exec, graph, 0);
+    if (ce != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return ib_cuda_fail(ce, "graph instantiate", __FILE__, __LINE__);
+    }
+    {
+        ProfToken tk = ib_prof_begin("adj2d_batch_graph_f32", cs);
+        IB_CUDA(cudaGraphLaunch(exec, cs));
+        ib_prof_end(tk, cs);
+        for (int64_t q = 0; q < nadj; ++q) {
+            ib_count_launch("adj2d_batch_f32");
+            ib_count_launch("leap2d_batch_seg_f32");
+        }
+    }
+    for (int i = 0; i < nshot; ++i) {
+        const Layout& L = ts[i]->L;
+        k_unpad<float><<<grid1(L.N, 256), 256, 0, cs>>>(L, grad[i], (float*)grads[i]);
+        ib_count_launch("setup");
+    }
+    IB_CHECK_LAUNCH("k_unpad");
+    IB_CUDA(cudaEventRecord(ready, cs));
+    IB_CUDA(cudaStreamWaitEvent(s, ready, 0));
+    IB_CUDA(cudaStreamSynchronize(cs));
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    cudaEventDestroy(ready);
+    cudaStreamDestroy(cs);
+    for (auto& b : keep) ib_free_bins(b);
     return IB_OK;
 }
 

@@ -23,7 +23,8 @@ EXPORTS = ["ib_opts_default", "ib_build_stencils", "ib_table_free", "ib_table_st
            "ib_last_error", "ib_version", "ib_profile_enable", "ib_profile_count", "ib_profile_get",
            "ib_forward_noalloc", "ib_mlp_create", "ib_mlp_free", "ib_mlp_info", "ib_mlp_buffers",
            "ib_mlp_sync_weights", "ib_mlp_features", "ib_mlp_forward", "ib_mlp_train_step",
-           "ib_mlp_targets", "ib_build_stencils_learned", "ib_table_learned"]
+           "ib_mlp_targets", "ib_build_stencils_learned", "ib_table_learned", "ib_forward_batch_ckpt",
+           "ib_adjoint_batch"]
 
 
 class IbError(RuntimeError):
@@ -97,6 +98,12 @@ def load(path=LIB_PATH):
     L.ib_adjoint.restype = i32
     L.ib_forward_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Shot), i32, i32, dbl, i32, vp]
     L.ib_forward_batch.restype = i32
+    L.ib_forward_batch_ckpt.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Shot), i32, i32, dbl, i32,
+                                        ctypes.POINTER(vp), i32, vp]
+    L.ib_forward_batch_ckpt.restype = i32
+    L.ib_adjoint_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Shot), i32, i32, dbl, i32,
+                                   ctypes.POINTER(vp), i32, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
+    L.ib_adjoint_batch.restype = i32
     L.ib_sync_status.argtypes = [vp]
     L.ib_sync_status.restype = i32
     L.ib_last_error.argtypes = []
@@ -431,6 +438,43 @@ def ib_forward_batch(tables, shots, dt, nt, stream=None):
         sh[i] = _shot(d["vel"], d.get("rho"), d["src"], d["rec"], d["wavelet"], tr)
     _check(load().ib_forward_batch(arr, sh, n, 32, float(dt), int(nt), _stream(stream)))
     return outs
+
+
+def _batch_shots(tables, shots, nt, need_traces=True):
+    n = len(tables)
+    arr = (ctypes.c_void_p * n)(*[t.handle.value for t in tables])
+    sh = (Shot * n)()
+    outs = []
+    for i, d in enumerate(shots):
+        tr = d.get("traces")
+        if tr is None and need_traces:
+            tr = torch.zeros((d["rec"].shape[0], nt), dtype=d["vel"].dtype, device=d["vel"].device)
+        outs.append(tr)
+        sh[i] = _shot(d["vel"], d.get("rho"), d["src"], d["rec"], d["wavelet"], tr)
+    return n, arr, sh, outs
+
+
+def _ptrs(tensors):
+    return (ctypes.c_void_p * len(tensors))(*[t.data_ptr() for t in tensors])
+
+
+def ib_forward_batch_ckpt(tables, shots, dt, nt, ckpts, n_ckpt, stream=None):
+    """ib_forward_batch that also fills ckpts[i] (uint8 device tensors of
+    ib_checkpoint_bytes(tables[i], 32, nt, n_ckpt) bytes)."""
+    n, arr, sh, outs = _batch_shots(tables, shots, nt)
+    _check(load().ib_forward_batch_ckpt(arr, sh, n, 32, float(dt), int(nt), _ptrs(ckpts), int(n_ckpt),
+                                        _stream(stream)))
+    return outs
+
+
+def ib_adjoint_batch(tables, shots, dt, nt, ckpts, n_ckpt, residuals, stream=None):
+    """Velocity gradients of all shots (list of float32 tensors, grid shape)."""
+    n, arr, sh, _ = _batch_shots(tables, shots, nt, need_traces=False)
+    grads = [torch.empty(t.shape, dtype=torch.float32, device=d["vel"].device) for t, d in zip(tables, shots)]
+    res = [r.contiguous() for r in residuals]
+    _check(load().ib_adjoint_batch(arr, sh, n, 32, float(dt), int(nt), _ptrs(ckpts), int(n_ckpt), _ptrs(res),
+                                   _ptrs(grads), _stream(stream)))
+    return grads
 
 
 def ib_sync_status(stream=None):

@@ -308,6 +308,37 @@ def test_forward_batch_matches_single_shots():
     assert rel_l2(outs[0].double().cpu().numpy(), ref) < TOL32
 
 
+def test_adjoint_batch_matches_single_shots():
+    """Shots of different sizes run through ib_forward_batch_ckpt and
+    ib_adjoint_batch (one graph for the backward pass) give the traces and the
+    velocity gradients of separate ib_forward / ib_adjoint calls; the batched
+    checkpoints also serve the single-shot adjoint (same layout)."""
+    nt, n_ckpt = 240, 7                   # segments of 35 steps, the last one short
+    shots, tables = [], []
+    for k in range(3):
+        w = inputs.workload_shot2d(10 + k, nt=nt, side=(120, 200))
+        t = ib.ib_build_stencils(cuda(w["sdf"]), w["h"], "free", "second", w["M"])
+        tables.append(t)
+        shots.append(dict(vel=cuda(w["vel"], torch.float32), wavelet=cuda(w["wavelet"], torch.float32),
+                          src=cuda(w["src"]), rec=cuda(w["rec"]), w=w))
+    dt = shots[0]["w"]["dt"]
+    ckpts = [torch.empty(ib.ib_checkpoint_bytes(t, 32, nt, n_ckpt), dtype=torch.uint8, device="cuda")
+             for t in tables]
+    outs = ib.ib_forward_batch_ckpt(tables, shots, dt, nt, ckpts, n_ckpt)
+    grads = ib.ib_adjoint_batch(tables, shots, dt, nt, ckpts, n_ckpt, outs)
+    ib.ib_sync_status()
+    for t, sh, tr, gb, ck in zip(tables, shots, outs, grads, ckpts):
+        ck1 = torch.empty_like(ck)
+        single = ib.ib_forward(t, sh["vel"], sh["wavelet"], sh["src"], sh["rec"], dt, nt, ckpt=ck1, n_ckpt=n_ckpt)
+        assert rel_l2(tr.double().cpu().numpy(), single.double().cpu().numpy()) < 2e-6
+        g1, _ = ib.ib_adjoint(t, sh["vel"], sh["wavelet"], sh["src"], sh["rec"], dt, nt, ck1, n_ckpt, single)
+        gref = g1.double().cpu().numpy()
+        assert np.abs(gref).max() > 0
+        assert rel_l2(gb.double().cpu().numpy(), gref) < 1e-5
+        g2, _ = ib.ib_adjoint(t, sh["vel"], sh["wavelet"], sh["src"], sh["rec"], dt, nt, ck, n_ckpt, tr)
+        assert rel_l2(g2.double().cpu().numpy(), gref) < 1e-5
+
+
 def test_forward_3d_tma_matches_plain_loads(monkeypatch):
     """FP32 3D runs through the TMA-staged kernel by default; IB_NO_TMA=1 selects
     the kernel with plain loads.  Both must give the same traces (nz = 34 also
