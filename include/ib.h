@@ -387,6 +387,16 @@ int32_t ib_profile_count(void);
 ib_status ib_profile_get(int32_t i, char* name, int32_t name_len, int64_t* launches,
                          int64_t* sampled, double* sampled_ms);
 
+/*
+ * ib_selftest_bounded_wait -- diagnostics hook (no counterpart in the paper).
+ * Runs one kernel that waits on a shared-memory barrier nothing will complete,
+ * with the iteration bound the TMA step kernels use.  The wait gives up, the
+ * kernel reports it, and the call returns IB_ERR_TIMEOUT with the context still
+ * usable -- the path a stalled copy takes in ib_forward.  IB_OK would mean the
+ * bound did not work.  Synchronises the stream.
+ */
+ib_status ib_selftest_bounded_wait(void* stream);
+
 /* Synchronise `stream` and return IB_ERR_CUDA on a pending device error. */
 ib_status ib_sync_status(void* stream);
 

@@ -455,11 +455,34 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* tm, in
         : "memory");
 }
 
-// bounded wait; returns false on timeout
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// bounded wait; returns false once about one second has passed (or after 2^22
+// polls, should the global timer not advance)
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-    for (int it = 0; it < (1 << 22); ++it)
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    for (int it = 0; it < (1 << 22); ++it) {
         if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > 1000000000ull) break;
+    }
     return false;
+}
+
+// Self-test of the bounded wait: one thread arms an mbarrier for bytes that no
+// copy will ever deliver and waits with the same bound as the TMA kernels; the
+// wait gives up and the kernel reports it through the error word.
+__global__ void k_wait_selftest(int* err) {
+    __shared__ alignas(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_expect_tx(&bar, 16);
+    if (!mbar_wait_bounded(&bar, 0)) atomicExch(err, 1);
 }
 
 template <int H>
@@ -2476,6 +2499,24 @@ extern "C" ib_status ib_adjoint_batch(const ib_table* const* tables, const ib_sh
     cudaEventDestroy(ready);
     cudaStreamDestroy(cs);
     for (auto& b : keep) ib_free_bins(b);
+    return IB_OK;
+}
+
+extern "C" ib_status ib_selftest_bounded_wait(void* stream) {
+    ib_set_error("");
+    cudaStream_t s = (cudaStream_t)stream;
+    Scratch S(s);
+    int* err;
+    TRY(S.alloc(&err, 1, true));
+    k_wait_selftest<<<1, 32, 0, s>>>(err);
+    IB_CHECK_LAUNCH("k_wait_selftest");
+    int h = 0;
+    IB_CUDA(cudaMemcpyAsync(&h, err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    IB_CUDA(cudaStreamSynchronize(s));
+    if (h) {
+        ib_set_error("bounded device wait gave up (self-test: expected)");
+        return IB_ERR_TIMEOUT;
+    }
     return IB_OK;
 }
 

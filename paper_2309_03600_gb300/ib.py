@@ -24,7 +24,7 @@ EXPORTS = ["ib_opts_default", "ib_build_stencils", "ib_table_free", "ib_table_st
            "ib_forward_noalloc", "ib_mlp_create", "ib_mlp_free", "ib_mlp_info", "ib_mlp_buffers",
            "ib_mlp_sync_weights", "ib_mlp_features", "ib_mlp_forward", "ib_mlp_train_step",
            "ib_mlp_targets", "ib_build_stencils_learned", "ib_table_learned", "ib_forward_batch_ckpt",
-           "ib_adjoint_batch"]
+           "ib_adjoint_batch", "ib_selftest_bounded_wait"]
 
 
 class IbError(RuntimeError):
@@ -104,6 +104,8 @@ def load(path=LIB_PATH):
     L.ib_adjoint_batch.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(Shot), i32, i32, dbl, i32,
                                    ctypes.POINTER(vp), i32, ctypes.POINTER(vp), ctypes.POINTER(vp), vp]
     L.ib_adjoint_batch.restype = i32
+    L.ib_selftest_bounded_wait.argtypes = [vp]
+    L.ib_selftest_bounded_wait.restype = i32
     L.ib_sync_status.argtypes = [vp]
     L.ib_sync_status.restype = i32
     L.ib_last_error.argtypes = []
@@ -475,6 +477,11 @@ def ib_adjoint_batch(tables, shots, dt, nt, ckpts, n_ckpt, residuals, stream=Non
     _check(load().ib_adjoint_batch(arr, sh, n, 32, float(dt), int(nt), _ptrs(ckpts), int(n_ckpt), _ptrs(res),
                                    _ptrs(grads), _stream(stream)))
     return grads
+
+
+def ib_selftest_bounded_wait(stream=None):
+    """Status of the bounded-wait self-test (IB_ERR_TIMEOUT when the bound works)."""
+    return load().ib_selftest_bounded_wait(_stream(stream))
 
 
 def ib_sync_status(stream=None):
