@@ -296,6 +296,192 @@ __global__ void __launch_bounds__(256) k_leap2d_batch(const StepArgs<T>* __restr
     leap2d_tile<T, H, TX, TZ>(a, local % a.ntx, local / a.ntx, tile, acc, sadd);
 }
 
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// A strip 64 wide and up to NSUB tiles of 64 x 8 deep, marched in z with D tiles
+// in flight.  Everything a tile reads arrives by 16-byte cp.async: the strip's
+// rows of p (columns x0-4 .. x0+67; x0-4 is a multiple of 4 because the row pitch
+// is a multiple of 32) into a buffer that holds the whole strip, p_prev and K into
+// D+1 stages.  Each thread owns two vertically adjacent points of every tile and
+// walks a pointer down its column, so the stencil's shared-memory offsets are
+// immediates.  Arithmetic per point is that of leap2d_tile.
+template <int H, int NSUB, int D>
+struct Strip2D {
+    static constexpr int TX = 64, TZ = 8, W = TX + 8, CH = W / 4, ROWS = NSUB * TZ + 2 * H;
+    static_assert(H <= 4 && TZ * CH <= 256 && 2 * H <= TZ, "one chunk per thread and tile");
+    float rows[ROWS][W];   // row j holds z = zs - H + j
+    float pm[D + 1][TZ * TX];
+    float kh[D + 1][TZ * TX];
+    float acc[TZ * TX];
+    float sadd[TZ * TX];
+};
+
+template <int H, int NSUB, int D>
+__device__ __forceinline__ void leap2d_strip(const StepArgs<float>& a, int64_t bx, int64_t bzc,
+                                             Strip2D<H, NSUB, D>& sm) {
+    using S = Strip2D<H, NSUB, D>;
+    constexpr int TX = S::TX, TZ = S::TZ, W = S::W, CH = S::CH;
+    const int tid = threadIdx.x;
+    const Layout& L = a.L;
+    const int64_t ntz = (L.nz + TZ - 1) / TZ;
+    const int64_t bz0 = bzc * NSUB;
+    const int nsub = (int)(ntz - bz0 < NSUB ? ntz - bz0 : NSUB);
+    const int64_t x0 = bx * TX, zs = bz0 * TZ;
+    // this thread's copies: chunk (pr, pc) of each tile's new rows of p (tid < TZ * CH);
+    // chunk (qr, qc) of p_prev (tid < 128) or of K (tid >= 128)
+    const int pr = tid / CH, pc = tid - pr * CH;
+    const bool pcopy = tid < TZ * CH;
+    const int qr = (tid & 127) >> 4, qc = tid & 15;
+    const float* qsrc = tid < 128 ? a.pm : a.Kh;
+    float* qdst = (tid < 128 ? &sm.pm[0][0] : &sm.kh[0][0]) + qr * TX + 4 * qc;
+    auto copy_row = [&](int j) {   // strip row j, chunk pc
+        const int64_t z = zs - H + j;
+        const int64_t q = (z + H + 1) * L.px + x0 - 4 + 4 * pc;
+        const bool ok = z < L.nz + H && q + 4 <= L.total;
+        cp_async<16>(&sm.rows[j][4 * pc], ok ? a.p + q : a.p, ok);
+    };
+    // group t: tile t's new rows of p (all of rows 0 .. TZ + 2H - 1 for t = 0), p_prev, K.
+    // A chunk that would end past the allocation is zero-filled; it feeds no stored point.
+    auto issue = [&](int t) {
+        if (t < nsub) {
+            if (pcopy) {
+                if (t == 0) {
+                    copy_row(pr);
+                    if (pr < 2 * H) copy_row(pr + TZ);
+                } else {
+                    copy_row(t * TZ + 2 * H + pr);
+                }
+            }
+            const int64_t z = zs + t * TZ + qr;
+            const int64_t q = (z + H + 1) * L.px + x0 + 4 * qc;
+            const bool ok = z < L.nz && q + 4 <= L.total;
+            cp_async<16>(qdst + (t % (D + 1)) * (TZ * TX), ok ? qsrc + q : qsrc, ok);
+        }
+        cp_async_commit();   // empty groups keep the count uniform
+    };
+    const int lx = tid & (TX - 1), lz0 = 2 * (tid >> 6);
+    const int i0 = lz0 * TX + lx;
+    sm.sadd[i0] = 0.f;
+    sm.sadd[i0 + TX] = 0.f;
+#pragma unroll
+    for (int t = 0; t < D; ++t) issue(t);
+    int32_t e0 = 0, e1 = 0;
+    if (a.op.ptr) {
+        e0 = a.op.ptr[bz0 * a.op.ntx + bx];
+        e1 = a.op.ptr[bz0 * a.op.ntx + bx + 1];
+    }
+    const float wv = a.src.n ? a.wavelet[a.step] : 0.f;
+    const float* colp = &sm.rows[lz0][lx + 4];   // this thread's column, tile s
+    const bool xin = x0 + lx < L.nx;
+    float* outp = a.out + (zs + lz0 + H + 1) * L.px + x0 + lx;
+    int st = 0;                                   // stage of tile s
+#pragma unroll 1
+    for (int s = 0; s < nsub; ++s, colp += TZ * W, outp += TZ * L.px, st = (st == D ? 0 : st + 1)) {
+        const int64_t z0 = zs + s * TZ;
+        const int64_t origin = L.base + z0 * L.px + x0;
+        cp_async_wait_group<D - 1>();
+        __syncthreads();   // tile s has landed; tile s - 1 is done with its buffers
+        issue(s + D);
+        int32_t f0 = 0, f1 = 0;
+        if (s + 1 < nsub && a.op.ptr) {
+            f0 = a.op.ptr[(bz0 + s + 1) * a.op.ntx + bx];
+            f1 = a.op.ptr[(bz0 + s + 1) * a.op.ntx + bx + 1];
+        }
+        // rows z0 + lz0 - H .. z0 + lz0 + 1 + H of this thread's column
+        float v[2 * H + 2];
+#pragma unroll
+        for (int m = 0; m < 2 * H + 2; ++m) v[m] = colp[m * W];
+        float cv[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const float* r0 = colp + (H + j) * W;
+            const float c = v[H + j];
+            float sum = 0.f;
+#pragma unroll
+            for (int k = 1; k <= H; ++k)
+                sum += a.w2[k] * (((r0[k] - c) + (r0[-k] - c)) + ((v[H + j + k] - c) + (v[H + j - k] - c)));
+            sm.acc[i0 + j * TX] = sum;
+            cv[j] = c;
+        }
+        tile_sources<float, TX, TZ>(a.src, wv, origin, L.px, sm.sadd, tid);
+        __syncthreads();
+        if (e1 > e0) {
+            add_entries_range(a.op, e0, e1, a.p, origin, sm.acc, tid, 256);
+            __syncthreads();
+        }
+        const float* pmS = sm.pm[st];
+        const float* khS = sm.kh[st];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int i = i0 + j * TX;
+            if (xin && z0 + lz0 + j < L.nz) {
+                const float c = cv[j];
+                outp[j * L.px] = c + ((c - pmS[i]) + khS[i] * sm.acc[i]) + sm.sadd[i];
+            }
+            sm.sadd[i] = 0.f;
+        }
+        e0 = f0;
+        e1 = f1;
+    }
+    cp_async_wait_group<0>();   // the empty groups past the strip's end
+}
+
+// many shots in one launch, each block a z-marched strip (leap2d_strip)
+template <int H, int NSUB, int D, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_leap2d_batch_m(const StepArgs<float>* __restrict__ shots,
+                                                              const int64_t* __restrict__ tile0,
+                                                              const int32_t* __restrict__ shot_of, int nshot,
+                                                              int step) {
+    __shared__ __align__(16) Strip2D<H, NSUB, D> sm;
+    const int64_t b = blockIdx.x;
+    const int lo = shot_of[b];
+    StepArgs<float> a = shots[lo];
+    const int64_t local = b - tile0[lo];
+    float* cur = (step & 1) ? a.buf1 : a.buf0;
+    float* prev = (step & 1) ? a.buf0 : a.buf1;
+    a.p = cur;
+    a.pm = prev;
+    a.out = prev;
+    a.step = step;
+    a.rec_step = step - 1;
+    record_receivers(a.rec, a.p, a.traces, a.nt, a.rec_step, local * 256 + threadIdx.x);
+    if (local >= a.ntiles) return;   // uniform per block
+    leap2d_strip<H, NSUB, D>(a, local % a.ntx, local / a.ntx, sm);
+}
+
+// one shot, FP32: block (x, y) is the z-marched strip of column x and chunk y
+template <int H, int NSUB, int D>
+__global__ void __launch_bounds__(256, 4) k_leap2d_m(StepArgs<float> a) {
+    __shared__ __align__(16) Strip2D<H, NSUB, D> sm;
+    const int64_t blk = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+    record_receivers(a.rec, a.p, a.traces, a.nt, a.rec_step, blk * 256 + threadIdx.x);
+    leap2d_strip<H, NSUB, D>(a, blockIdx.x, blockIdx.y, sm);
+}
+
+// batched recompute step (as k_leap2d_batch_seg) on z-marched strips; the block
+// map counts strips, ntx * ceil(ceil(nz / 8) / NSUB) per shot
+template <int H, int NSUB, int D>
+__global__ void __launch_bounds__(256, 4) k_leap2d_batch_seg_m(const StepArgs<float>* __restrict__ shots,
+                                                               const int64_t* __restrict__ tile0,
+                                                               const int32_t* __restrict__ shot_of, int n, int j) {
+    __shared__ __align__(16) Strip2D<H, NSUB, D> sm;
+    const int64_t b = blockIdx.x;
+    const int sh = shot_of[b];
+    StepArgs<float> a = shots[sh];
+    const int64_t local = b - tile0[sh];
+    const int64_t nstrip = a.ntx * (((a.L.nz + 7) / 8 + NSUB - 1) / NSUB);
+    if (local >= nstrip) return;   // uniform per block
+    const int64_t tot = a.L.total;
+    a.p = a.buf0 + (int64_t)(j + 1) * tot;
+    a.pm = a.buf0 + (int64_t)j * tot;
+    a.out = a.buf0 + (int64_t)(j + 2) * tot;
+    a.step = n;
+    leap2d_strip<H, NSUB, D>(a, local % a.ntx, local / a.ntx, sm);
+}
+
 // Batched recompute step n of a checkpoint segment: the shot's segment buffer
 // (buf0) holds p^{c-1+j} in slot j, and step n = c + j writes slot j + 2.
 template <typename T, int H, int TX, int TZ>
@@ -1357,6 +1543,20 @@ extern "C" int64_t ib_checkpoint_bytes(const ib_table* t, int32_t precision, int
     return (int64_t)n_ckpt * 2 * t->L.total * es;
 }
 
+static const int STRIP_NSUB = 8, STRIP_D = 3;   // z-marched strips: 8 tiles of 64 x 8, 3 in flight
+
+// One FP32 shot runs on strips when there are enough of them to fill the GPU
+// (a strip is 8 tiles of work: on small grids the tile kernel keeps more blocks
+// in flight).  IB_STRIP=0 / IB_STRIP=1 turn strips off / on whatever the size.
+// Strips are used only when their blocks cover the receivers.
+static bool use_strips(const Layout& L, int64_t nrec) {
+    const int64_t nblk = ((L.nx + TX2 - 1) / TX2) * (((L.nz + TZ2 - 1) / TZ2 + STRIP_NSUB - 1) / STRIP_NSUB);
+    if (nblk * 256 < nrec) return false;
+    const char* e = getenv("IB_STRIP");
+    if (e && *e) return e[0] != '0';
+    return nblk >= 1024;
+}
+
 template <typename T>
 static void launch_leap2d(const StepArgs<T>& a, int H, dim3 grid, cudaStream_t s) {
     PROF_LAUNCH(kname<T>("leap2d_f32", "leap2d_f64"), s, {
@@ -1364,6 +1564,15 @@ static void launch_leap2d(const StepArgs<T>& a, int H, dim3 grid, cudaStream_t s
         else if (H == 2) k_leap2d<T, 2, TX2, TZ2><<<grid, 256, 0, s>>>(a);
         else if (H == 3) k_leap2d<T, 3, TX2, TZ2><<<grid, 256, 0, s>>>(a);
         else k_leap2d<T, 4, TX2, TZ2><<<grid, 256, 0, s>>>(a);
+    });
+}
+
+static void launch_leap2d_strip(const StepArgs<float>& a, int H, dim3 grid, cudaStream_t s) {
+    PROF_LAUNCH("leap2d_strip_f32", s, {
+        if (H == 1) k_leap2d_m<1, STRIP_NSUB, STRIP_D><<<grid, 256, 0, s>>>(a);
+        else if (H == 2) k_leap2d_m<2, STRIP_NSUB, STRIP_D><<<grid, 256, 0, s>>>(a);
+        else if (H == 3) k_leap2d_m<3, STRIP_NSUB, STRIP_D><<<grid, 256, 0, s>>>(a);
+        else k_leap2d_m<4, STRIP_NSUB, STRIP_D><<<grid, 256, 0, s>>>(a);
     });
 }
 
@@ -1405,6 +1614,9 @@ static ib_status forward_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, 
     T* cur = p0;   // p^n
     T* prev = p1;  // p^{n-1}
     dim3 grid2((unsigned)((L.nx + TX2 - 1) / TX2), (unsigned)((L.nz + TZ2 - 1) / TZ2));
+    const bool strips = d == 2 && sizeof(T) == 4 && use_strips(L, g.rec.n);
+    dim3 grids((unsigned)((L.nx + TX2 - 1) / TX2),
+               (unsigned)(((L.nz + TZ2 - 1) / TZ2 + STRIP_NSUB - 1) / STRIP_NSUB));
     const int zchunk = 32;
     dim3 grid3((unsigned)((L.nx + 31) / 32), (unsigned)((L.ny + 7) / 8), (unsigned)((L.nz + zchunk - 1) / zchunk));
     const int64_t nty3 = (L.ny + 7) / 8;
@@ -1428,7 +1640,9 @@ static ib_status forward_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, 
         a.out = prev;
         a.step = n;
         a.rec_step = n - 1;
-        if (d == 2) {
+        if (strips) {
+            launch_leap2d_strip(*reinterpret_cast<const StepArgs<float>*>(&a), H, grids, s);
+        } else if (d == 2) {
             launch_leap2d<T>(a, H, grid2, s);
         } else if (use_tma) {
             dim3 blk(32, 8);
@@ -2036,15 +2250,23 @@ extern "C" ib_status ib_adjoint(const ib_table* tc, const ib_shot* sh, int32_t p
 // timing the candidates on the batch itself (cached per shape class)
 // ---------------------------------------------------------------------------
 struct TileShape {
-    int tx, tz;
+    int tx, tz, nsub;   // nsub > 1: z-marched strips of nsub tiles (k_leap2d_batch_m)
 };
-static const TileShape kShapes[4] = {{64, 8}, {32, 16}, {128, 4}, {64, 4}};
+static const int kNumShapes = 8;
+static const TileShape kShapes[kNumShapes] = {{64, 8, 1}, {32, 16, 1}, {128, 4, 1}, {64, 4, 1},
+                                              {64, 8, 8}, {64, 8, 8}, {64, 8, 8}, {64, 8, 8}};
 
 template <int H, int TX, int TZ>
 static void launch_batch(const StepArgs<float>* args, const int64_t* tile0, const int32_t* shot_of, int nshot,
                          int step, int64_t nblk,
                          cudaStream_t s) {
     k_leap2d_batch<float, H, TX, TZ><<<(unsigned)nblk, 256, 0, s>>>(args, tile0, shot_of, nshot, step);
+}
+
+template <int H, int NSUB, int D, int MINB>
+static void launch_batch_m(const StepArgs<float>* args, const int64_t* tile0, const int32_t* shot_of, int nshot,
+                           int step, int64_t nblk, cudaStream_t s) {
+    k_leap2d_batch_m<H, NSUB, D, MINB><<<(unsigned)nblk, 256, 0, s>>>(args, tile0, shot_of, nshot, step);
 }
 
 template <int H>
@@ -2055,7 +2277,11 @@ static void launch_batch_shape(int si, const StepArgs<float>* args, const int64_
         case 0: launch_batch<H, 64, 8>(args, tile0, shot_of, nshot, step, nblk, s); break;
         case 1: launch_batch<H, 32, 16>(args, tile0, shot_of, nshot, step, nblk, s); break;
         case 2: launch_batch<H, 128, 4>(args, tile0, shot_of, nshot, step, nblk, s); break;
-        default: launch_batch<H, 64, 4>(args, tile0, shot_of, nshot, step, nblk, s); break;
+        case 3: launch_batch<H, 64, 4>(args, tile0, shot_of, nshot, step, nblk, s); break;
+        case 4: launch_batch_m<H, 8, 2, 4>(args, tile0, shot_of, nshot, step, nblk, s); break;
+        case 5: launch_batch_m<H, 8, 3, 4>(args, tile0, shot_of, nshot, step, nblk, s); break;
+        case 6: launch_batch_m<H, 8, 2, 5>(args, tile0, shot_of, nshot, step, nblk, s); break;
+        default: launch_batch_m<H, 8, 3, 5>(args, tile0, shot_of, nshot, step, nblk, s); break;
     }
 }
 
@@ -2109,7 +2335,8 @@ static ib_status batch_prepare(ib_table* const* ts, const ib_shot* shots, int ns
         a.buf0 = buf0[i];
         a.buf1 = buf1[i];
         a.ntx = (L.nx + tx - 1) / tx;
-        int64_t ntiles = a.ntx * ((L.nz + tz - 1) / tz);
+        const int nsub = kShapes[si].nsub;
+        int64_t ntiles = a.ntx * ((((L.nz + tz - 1) / tz) + nsub - 1) / nsub);
         a.ntiles = ntiles;
         // receivers are recorded by the first blocks of the shot: make sure there are enough
         int64_t need = (shots[i].nrec + 255) / 256;
@@ -2178,9 +2405,17 @@ static ib_status forward_batch_impl(const ib_table* const* tables, const ib_shot
         TRY(setup_points<float>(ts[i], &shots[i], dt * dt / pow(ts[i]->grid.h, 2), S, geo[i]));
         total += L.N;
     }
-    // ---- tile-shape autotuning (first batch of a shape class)
+    // ---- tile-shape autotuning (first batch of a shape class); IB_BATCH_SHAPE=<index
+    // into kShapes> fixes the shape instead
     int best = 0;
-    {
+    const char* forced = getenv("IB_BATCH_SHAPE");
+    if (forced && *forced) {
+        best = atoi(forced);
+        if (best < 0 || best >= kNumShapes) {
+            ib_set_error("IB_BATCH_SHAPE must name a tile shape index in [0, 8)");
+            return IB_ERR_ARG;
+        }
+    } else {
         std::pair<int, int64_t> key(H, total >> 18);
         bool have = false;
         {
@@ -2196,7 +2431,7 @@ static ib_status forward_batch_impl(const ib_table* const* tables, const ib_shot
             cudaEvent_t e0, e1;
             IB_CUDA(cudaEventCreate(&e0));
             IB_CUDA(cudaEventCreate(&e1));
-            for (int si = 0; si < 4; ++si) {
+            for (int si = 0; si < kNumShapes; ++si) {
                 BatchSetup B;
                 TRY(batch_prepare(ts.data(), shots, nshot, si, dt, nt, b0, b1, Kh, geo, S, B));
                 const int trial = std::min(nt, 12);
@@ -2311,13 +2546,17 @@ extern "C" ib_status ib_forward_batch_ckpt(const ib_table* const* tables, const 
 // batched adjoint: every shot's segments in lockstep, one graph for the whole
 // backward pass (segment restore, batched recompute steps, batched adjoint steps)
 // ---------------------------------------------------------------------------
+// block maps: tile0 / shot_of over 64 x 8 tiles (adjoint steps), stile0 / sshot_of
+// over z-marched strips (recompute steps)
 template <int H>
 static void launch_adj_batch_h(const StepArgs<float>* fargs, const AdjBatch<float>* aargs, const ShotCopy<float>* rst,
-                               const int64_t* tile0, const int32_t* shot_of, int64_t nblk, dim3 cgrid, int nt,
-                               int64_t c, int64_t e, int k, cudaStream_t s) {
+                               const int64_t* tile0, const int32_t* shot_of, int64_t nblk, const int64_t* stile0,
+                               const int32_t* sshot_of, int64_t nsblk, dim3 cgrid, int nt, int64_t c, int64_t e,
+                               int k, cudaStream_t s) {
     k_seg_restore_batch<float><<<cgrid, 256, 0, s>>>(rst, k);
     for (int64_t n = c; n < e; ++n)
-        k_leap2d_batch_seg<float, H, 64, 8><<<(unsigned)nblk, 256, 0, s>>>(fargs, tile0, shot_of, (int)n, (int)(n - c));
+        k_leap2d_batch_seg_m<H, STRIP_NSUB, STRIP_D><<<(unsigned)nsblk, 256, 0, s>>>(fargs, stile0, sshot_of, (int)n,
+                                                                                      (int)(n - c));
     for (int64_t m = e; m >= c + 1; --m)
         k_adj2d_batch<float, H, 64, 8><<<(unsigned)nblk, 256, 0, s>>>(aargs, tile0, shot_of, (int)m, (int)(m - c), nt);
 }
@@ -2362,7 +2601,7 @@ extern "C" ib_status ib_adjoint_batch(const ib_table* const* tables, const ib_sh
     std::vector<AdjBatch<float>> aargs(nshot);
     std::vector<ShotCopy<float>> rst(nshot);
     std::vector<float*> grad(nshot);
-    std::vector<int64_t> tile0(nshot + 1, 0);
+    std::vector<int64_t> tile0(nshot + 1, 0), stile0(nshot + 1, 0);
     std::vector<TileBins> keep;
     int64_t maxtot = 0;
     for (int i = 0; i < nshot; ++i) {
@@ -2423,22 +2662,29 @@ extern "C" ib_status ib_adjoint_batch(const ib_table* const* tables, const ib_sh
         aargs[i].seg = segbuf;
         rst[i] = {(const float*)ckpts[i], nullptr, segbuf, L.total};
         tile0[i + 1] = tile0[i] + fa.ntiles;
+        stile0[i + 1] = stile0[i] + fa.ntx * (((L.nz + TZ2 - 1) / TZ2 + STRIP_NSUB - 1) / STRIP_NSUB);
         maxtot = std::max(maxtot, L.total);
     }
-    const int64_t nblk = tile0[nshot];
-    std::vector<int32_t> shot_of(nblk);
-    for (int i = 0; i < nshot; ++i)
+    const int64_t nblk = tile0[nshot], nsblk = stile0[nshot];
+    std::vector<int32_t> shot_of(nblk), sshot_of(nsblk);
+    for (int i = 0; i < nshot; ++i) {
         for (int64_t b = tile0[i]; b < tile0[i + 1]; ++b) shot_of[b] = i;
+        for (int64_t b = stile0[i]; b < stile0[i + 1]; ++b) sshot_of[b] = i;
+    }
     StepArgs<float>* d_f;
     AdjBatch<float>* d_a;
     ShotCopy<float>* d_r;
-    int64_t* d_t0;
-    int32_t* d_so;
+    int64_t *d_t0, *d_st0;
+    int32_t *d_so, *d_sso;
     TRY(S.alloc(&d_f, nshot));
     TRY(S.alloc(&d_a, nshot));
     TRY(S.alloc(&d_r, nshot));
     TRY(S.alloc(&d_t0, nshot + 1));
     TRY(S.alloc(&d_so, std::max<int64_t>(nblk, 1)));
+    TRY(S.alloc(&d_st0, nshot + 1));
+    TRY(S.alloc(&d_sso, std::max<int64_t>(nsblk, 1)));
+    IB_CUDA(cudaMemcpyAsync(d_st0, stile0.data(), 8 * (nshot + 1), cudaMemcpyHostToDevice, s));
+    IB_CUDA(cudaMemcpyAsync(d_sso, sshot_of.data(), 4 * nsblk, cudaMemcpyHostToDevice, s));
     IB_CUDA(cudaMemcpyAsync(d_f, fargs.data(), sizeof(StepArgs<float>) * nshot, cudaMemcpyHostToDevice, s));
     IB_CUDA(cudaMemcpyAsync(d_a, aargs.data(), sizeof(AdjBatch<float>) * nshot, cudaMemcpyHostToDevice, s));
     IB_CUDA(cudaMemcpyAsync(d_r, rst.data(), sizeof(ShotCopy<float>) * nshot, cudaMemcpyHostToDevice, s));
@@ -2462,10 +2708,10 @@ extern "C" ib_status ib_adjoint_batch(const ib_table* const* tables, const ib_sh
         if (c >= nt) continue;
         const int64_t e = std::min<int64_t>(c + seg, nt);
         switch (H) {
-            case 1: launch_adj_batch_h<1>(d_f, d_a, d_r, d_t0, d_so, nblk, cgrid, nt, c, e, k, cs); break;
-            case 2: launch_adj_batch_h<2>(d_f, d_a, d_r, d_t0, d_so, nblk, cgrid, nt, c, e, k, cs); break;
-            case 3: launch_adj_batch_h<3>(d_f, d_a, d_r, d_t0, d_so, nblk, cgrid, nt, c, e, k, cs); break;
-            default: launch_adj_batch_h<4>(d_f, d_a, d_r, d_t0, d_so, nblk, cgrid, nt, c, e, k, cs); break;
+            case 1: launch_adj_batch_h<1>(d_f, d_a, d_r, d_t0, d_so, nblk, d_st0, d_sso, nsblk, cgrid, nt, c, e, k, cs); break;
+            case 2: launch_adj_batch_h<2>(d_f, d_a, d_r, d_t0, d_so, nblk, d_st0, d_sso, nsblk, cgrid, nt, c, e, k, cs); break;
+            case 3: launch_adj_batch_h<3>(d_f, d_a, d_r, d_t0, d_so, nblk, d_st0, d_sso, nsblk, cgrid, nt, c, e, k, cs); break;
+            default: launch_adj_batch_h<4>(d_f, d_a, d_r, d_t0, d_so, nblk, d_st0, d_sso, nsblk, cgrid, nt, c, e, k, cs); break;
         }
         nadj += e - c;
     }
