@@ -157,7 +157,7 @@ typedef struct {
     const void* wavelet_dev;    /* [nt] source time function, sample n is used in
                                    the step that produces p^{n+1}                    */
     void* traces_dev;           /* [nrec][nt] output: trace[r][n] = p^{n+1} at r     */
-    int32_t nsrc;
+    int32_t nsrc;               /* 0 .. 32 (more: IB_ERR_ARG)                       */
     int32_t nrec;
 } ib_shot;
 

@@ -319,6 +319,11 @@ struct Strip2D {
     float sadd[TZ * TX];
 };
 
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, bool valid) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(dst), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
+
 template <int H, int NSUB, int D>
 __device__ __forceinline__ void leap2d_strip(const StepArgs<float>& a, int64_t bx, int64_t bzc,
                                              Strip2D<H, NSUB, D>& sm) {
@@ -330,21 +335,33 @@ __device__ __forceinline__ void leap2d_strip(const StepArgs<float>& a, int64_t b
     const int64_t bz0 = bzc * NSUB;
     const int nsub = (int)(ntz - bz0 < NSUB ? ntz - bz0 : NSUB);
     const int64_t x0 = bx * TX, zs = bz0 * TZ;
-    // this thread's copies: chunk (pr, pc) of each tile's new rows of p (tid < TZ * CH);
-    // chunk (qr, qc) of p_prev (tid < 128) or of K (tid >= 128)
+    const int64_t tstep = TZ * L.px;   // elements from one tile's rows to the next
+    // This thread's copies: chunk (pr, pc) of each tile's new rows of p (tid < TZ * CH)
+    // and chunk (qr, qc) of p_prev (tid < 128) or K (tid >= 128).  A chunk is zero-filled
+    // when its row is past the last row a stored point reads, or when it would end past
+    // the allocation; it feeds no stored point then.  The chunks move down tstep
+    // elements per tile: their offsets, rows and shared addresses are carried along.
     const int pr = tid / CH, pc = tid - pr * CH;
     const bool pcopy = tid < TZ * CH;
-    const int qr = (tid & 127) >> 4, qc = tid & 15;
-    const float* qsrc = tid < 128 ? a.pm : a.Kh;
-    float* qdst = (tid < 128 ? &sm.pm[0][0] : &sm.kh[0][0]) + qr * TX + 4 * qc;
-    auto copy_row = [&](int j) {   // strip row j, chunk pc
+    auto copy_row = [&](int j) {   // strip row j (tile 0 only)
         const int64_t z = zs - H + j;
         const int64_t q = (z + H + 1) * L.px + x0 - 4 + 4 * pc;
         const bool ok = z < L.nz + H && q + 4 <= L.total;
-        cp_async<16>(&sm.rows[j][4 * pc], ok ? a.p + q : a.p, ok);
+        cp_async16(smem_u32(&sm.rows[j][4 * pc]), ok ? a.p + q : a.p, ok);
     };
-    // group t: tile t's new rows of p (all of rows 0 .. TZ + 2H - 1 for t = 0), p_prev, K.
-    // A chunk that would end past the allocation is zero-filled; it feeds no stored point.
+    int64_t pq = (zs + TZ + 2 * H + pr + 1) * L.px + x0 - 4 + 4 * pc;   // tile 1: strip row TZ + 2H + pr
+    const int nzh = (int)(L.nz + H), nzi = (int)L.nz;   // row limits (2D rows < 2^31)
+    const int64_t qlim = L.total - 4;                 // last chunk start inside the allocation
+    int pz = (int)(zs + TZ + H + pr);
+    uint32_t pdst = smem_u32(&sm.rows[0][0]) + 4u * (uint32_t)((TZ + 2 * H + pr) * W + 4 * pc);
+    const int qr = (tid & 127) >> 4, qc = tid & 15;
+    const float* qsrc = tid < 128 ? a.pm : a.Kh;
+    int64_t qq = (zs + qr + H + 1) * L.px + x0 + 4 * qc;                // tile 0
+    int qz = (int)(zs + qr);
+    const uint32_t qdst0 = smem_u32((tid < 128 ? &sm.pm[0][0] : &sm.kh[0][0]) + qr * TX + 4 * qc);
+    int qst = 0;
+    // group t (issued in order t = 0, 1, ...): tile t's new rows of p (rows 0 .. TZ + 2H - 1
+    // for t = 0), its p_prev and K
     auto issue = [&](int t) {
         if (t < nsub) {
             if (pcopy) {
@@ -352,13 +369,18 @@ __device__ __forceinline__ void leap2d_strip(const StepArgs<float>& a, int64_t b
                     copy_row(pr);
                     if (pr < 2 * H) copy_row(pr + TZ);
                 } else {
-                    copy_row(t * TZ + 2 * H + pr);
+                    const bool ok = pz < nzh && pq <= qlim;
+                    cp_async16(pdst, ok ? a.p + pq : a.p, ok);
+                    pq += tstep;
+                    pz += TZ;
+                    pdst += 4u * TZ * W;
                 }
             }
-            const int64_t z = zs + t * TZ + qr;
-            const int64_t q = (z + H + 1) * L.px + x0 + 4 * qc;
-            const bool ok = z < L.nz && q + 4 <= L.total;
-            cp_async<16>(qdst + (t % (D + 1)) * (TZ * TX), ok ? qsrc + q : qsrc, ok);
+            const bool ok = qz < nzi && qq <= qlim;
+            cp_async16(qdst0 + 4u * TZ * TX * qst, ok ? qsrc + qq : qsrc, ok);
+            qq += tstep;
+            qz += TZ;
+            qst = qst == D ? 0 : qst + 1;
         }
         cp_async_commit();   // empty groups keep the count uniform
     };
@@ -368,27 +390,43 @@ __device__ __forceinline__ void leap2d_strip(const StepArgs<float>& a, int64_t b
     sm.sadd[i0 + TX] = 0.f;
 #pragma unroll
     for (int t = 0; t < D; ++t) issue(t);
-    int32_t e0 = 0, e1 = 0;
-    if (a.op.ptr) {
-        e0 = a.op.ptr[bz0 * a.op.ntx + bx];
-        e1 = a.op.ptr[bz0 * a.op.ntx + bx + 1];
-    }
+    // this thread's source corner (tid < 8 n) as (row, column) from the strip origin
+    int srow = -1, scol = 0;
+    float sw = 0.f;
     const float wv = a.src.n ? a.wavelet[a.step] : 0.f;
+    if (tid < 8 * a.src.n) {
+        const int64_t rel = a.src.idx[tid] - (L.base + zs * L.px + x0);
+        if (rel >= 0) {
+            const int64_t r = rel / L.px, c = rel - r * L.px;
+            if (r < NSUB * TZ && c < TX && a.src.w[tid] != 0.f) {
+                srow = (int)r;
+                scol = (int)c;
+                sw = a.src.w[tid] * wv;
+            }
+        }
+    }
+    const int32_t* pp = a.op.ptr ? a.op.ptr + bz0 * a.op.ntx + bx : nullptr;   // tile s's entry range
+    int32_t e0 = 0, e1 = 0;
+    if (pp) {
+        e0 = pp[0];
+        e1 = pp[1];
+    }
     const float* colp = &sm.rows[lz0][lx + 4];   // this thread's column, tile s
     const bool xin = x0 + lx < L.nx;
+    const int zleft = nzi - (int)zs - lz0;       // rows of this thread's column left to store
     float* outp = a.out + (zs + lz0 + H + 1) * L.px + x0 + lx;
+    int64_t origin = L.base + zs * L.px + x0;    // tile s
     int st = 0;                                   // stage of tile s
 #pragma unroll 1
-    for (int s = 0; s < nsub; ++s, colp += TZ * W, outp += TZ * L.px, st = (st == D ? 0 : st + 1)) {
-        const int64_t z0 = zs + s * TZ;
-        const int64_t origin = L.base + z0 * L.px + x0;
+    for (int s = 0; s < nsub; ++s) {
         cp_async_wait_group<D - 1>();
         __syncthreads();   // tile s has landed; tile s - 1 is done with its buffers
         issue(s + D);
         int32_t f0 = 0, f1 = 0;
-        if (s + 1 < nsub && a.op.ptr) {
-            f0 = a.op.ptr[(bz0 + s + 1) * a.op.ntx + bx];
-            f1 = a.op.ptr[(bz0 + s + 1) * a.op.ntx + bx + 1];
+        if (s + 1 < nsub && pp) {
+            pp += a.op.ntx;
+            f0 = pp[0];
+            f1 = pp[1];
         }
         // rows z0 + lz0 - H .. z0 + lz0 + 1 + H of this thread's column
         float v[2 * H + 2];
@@ -406,7 +444,10 @@ __device__ __forceinline__ void leap2d_strip(const StepArgs<float>& a, int64_t b
             sm.acc[i0 + j * TX] = sum;
             cv[j] = c;
         }
-        tile_sources<float, TX, TZ>(a.src, wv, origin, L.px, sm.sadd, tid);
+        {
+            const int ly = srow - s * TZ;
+            if (srow >= 0 && ly >= 0 && ly < TZ) atomicAdd(&sm.sadd[ly * TX + scol], sw);
+        }
         __syncthreads();
         if (e1 > e0) {
             add_entries_range(a.op, e0, e1, a.p, origin, sm.acc, tid, 256);
@@ -417,7 +458,7 @@ __device__ __forceinline__ void leap2d_strip(const StepArgs<float>& a, int64_t b
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
             const int i = i0 + j * TX;
-            if (xin && z0 + lz0 + j < L.nz) {
+            if (xin && s * TZ + j < zleft) {
                 const float c = cv[j];
                 outp[j * L.px] = c + ((c - pmS[i]) + khS[i] * sm.acc[i]) + sm.sadd[i];
             }
@@ -425,6 +466,10 @@ __device__ __forceinline__ void leap2d_strip(const StepArgs<float>& a, int64_t b
         }
         e0 = f0;
         e1 = f1;
+        colp += TZ * W;
+        outp += tstep;
+        origin += tstep;
+        st = st == D ? 0 : st + 1;
     }
     cp_async_wait_group<0>();   // the empty groups past the strip's end
 }
@@ -1494,8 +1539,10 @@ static ib_status check_shot(const ib_table* t, const ib_shot* sh, int precision,
         ib_set_error("missing shot arrays");
         return IB_ERR_ARG;
     }
-    if (sh->nsrc > 64) {
-        ib_set_error("at most 64 sources per shot");
+    if (sh->nsrc > 32) {
+        // the step kernels spread each source over its 8 interpolation corners with
+        // one thread per corner of a 256-thread block
+        ib_set_error("at most 32 sources per shot");
         return IB_ERR_ARG;
     }
     return IB_OK;

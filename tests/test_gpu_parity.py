@@ -283,6 +283,24 @@ def test_argument_errors():
         ib.ib_forward(t, v, cuda(np.zeros(5)), cuda(np.zeros((1, 2))), cuda(np.zeros((1, 2))), -1.0, 5)
 
 
+def test_forward_many_sources():
+    """32 off-grid sources (the most a shot may have, 256 interpolation corners)
+    all enter the FP64 traces as in the oracle; a 33rd is an argument error."""
+    w = inputs.workload_flat2d(nx=81, nz=71, nt=150, z0_cells=20.3, src_cells=(40.0, 45.0),
+                               rec_x_cells=(10, 70), rec_z_cells=30)
+    rng = np.random.default_rng(7)
+    src = np.stack([rng.uniform(5.0, 75.0, 32) * w["h"], rng.uniform(28.0, 65.0, 32) * w["h"]], axis=1)
+    t = ib.ib_build_stencils(cuda(w["sdf"]), w["h"], "free", "second", w["M"])
+    tr = ib.ib_forward(t, cuda(w["vel"]), cuda(w["wavelet"]), cuda(src), cuda(w["rec"]), w["dt"], 150)
+    ref = sim.Leapfrog(w["sdf"], w["vel"], w["h"], w["M"], "free", w["dt"], src, w["rec"]).forward(w["wavelet"], 150)
+    assert np.abs(ref).max() > 0
+    assert rel_l2(tr.cpu().numpy(), ref) < TOL64
+    src33 = np.concatenate([src, src[:1]], axis=0)
+    with pytest.raises(ib.IbError) as e:
+        ib.ib_forward(t, cuda(w["vel"]), cuda(w["wavelet"]), cuda(src33), cuda(w["rec"]), w["dt"], 150)
+    assert e.value.status == ib.IB_ERR_ARG
+
+
 # ---------------------------------------------------------------------------
 # batched shots
 # ---------------------------------------------------------------------------
