@@ -506,8 +506,10 @@ __global__ void __launch_bounds__(256, 4) k_leap2d_m(StepArgs<float> a) {
     leap2d_strip<H, NSUB, D>(a, blockIdx.x, blockIdx.y, sm);
 }
 
-// batched recompute step (as k_leap2d_batch_seg) on z-marched strips; the block
-// map counts strips, ntx * ceil(ceil(nz / 8) / NSUB) per shot
+// Batched recompute step n of a checkpoint segment, on z-marched strips: the
+// shot's segment buffer (buf0) holds p^{c-1+j} in slot j, and step n = c + j
+// writes slot j + 2.  The block map counts strips, ntx * ceil(ceil(nz / 8) / NSUB)
+// per shot.
 template <int H, int NSUB, int D>
 __global__ void __launch_bounds__(256, 4) k_leap2d_batch_seg_m(const StepArgs<float>* __restrict__ shots,
                                                                const int64_t* __restrict__ tile0,
@@ -525,28 +527,6 @@ __global__ void __launch_bounds__(256, 4) k_leap2d_batch_seg_m(const StepArgs<fl
     a.out = a.buf0 + (int64_t)(j + 2) * tot;
     a.step = n;
     leap2d_strip<H, NSUB, D>(a, local % a.ntx, local / a.ntx, sm);
-}
-
-// Batched recompute step n of a checkpoint segment: the shot's segment buffer
-// (buf0) holds p^{c-1+j} in slot j, and step n = c + j writes slot j + 2.
-template <typename T, int H, int TX, int TZ>
-__global__ void __launch_bounds__(256) k_leap2d_batch_seg(const StepArgs<T>* __restrict__ shots,
-                                                          const int64_t* __restrict__ tile0,
-                                                          const int32_t* __restrict__ shot_of, int n, int j) {
-    __shared__ T tile[TZ + 2 * H][TX + 2 * H];
-    __shared__ T acc[TZ * TX];
-    __shared__ T sadd[TZ * TX];
-    const int64_t b = blockIdx.x;
-    const int sh = shot_of[b];
-    StepArgs<T> a = shots[sh];
-    const int64_t local = b - tile0[sh];
-    if (local >= a.ntiles) return;   // uniform per block
-    const int64_t tot = a.L.total;
-    a.p = a.buf0 + (int64_t)(j + 1) * tot;
-    a.pm = a.buf0 + (int64_t)j * tot;
-    a.out = a.buf0 + (int64_t)(j + 2) * tot;
-    a.step = n;
-    leap2d_tile<T, H, TX, TZ>(a, local % a.ntx, local / a.ntx, tile, acc, sadd);
 }
 
 // Per-shot field copies between wavefield buffers, checkpoints and segment buffers
