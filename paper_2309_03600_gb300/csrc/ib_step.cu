@@ -1180,23 +1180,28 @@ struct AdjArgs {
 
 // one adjoint tile (bx, bz); shared arrays from the calling kernel
 template <typename T, int H, int TX, int TZ>
-__device__ __forceinline__ void adj2d_tile(const AdjArgs<T>& a, int64_t bx, int64_t bz, T (*tile)[TX + 2 * H], T* tmu,
+__device__ __forceinline__ void adj2d_tile(const AdjArgs<T>& a, int64_t bx, int64_t bz, T (*tile)[TX + 8], T* tmu,
                                            T* acc, T* sw) {
     static_assert((TZ * TX) % 256 == 0, "whole points per thread");
-    constexpr int PT = TZ * TX / 256, NT = (TZ + 2 * H) * (TX + 2 * H);
+    constexpr int W = TX + 8, V = 16 / (int)sizeof(T), CHR = W / V;
+    constexpr int PT = TZ * TX / 256, NT = (TZ + 2 * H) * W;
+    static_assert(H <= 4 && TX % 64 == 0, "columns x0-4 .. x0+TX+3 in 16-byte chunks");
     const int tid = threadIdx.x;
     const int64_t x0 = bx * TX, z0 = bz * TZ;
     const Layout& L = a.L;
     const int64_t origin = L.base + z0 * L.px + x0;
     const int64_t tile_id = bz * a.opT.ntx + bx;
-    // K and mu halo tiles arrive by cp.async ...
-    for (int i = tid; i < NT; i += 256) {
-        const int lz = i / (TX + 2 * H), lx = i - lz * (TX + 2 * H);
-        const int64_t x = x0 + lx - H, z = z0 + lz - H;
-        const bool ok = x < L.nx + H && z < L.nz + H;
-        const int64_t q = ok ? L.base + z * L.px + x : 0;
-        cp_async<(int)sizeof(T)>(&tile[lz][lx], a.Kh + q, ok);
-        cp_async<(int)sizeof(T)>(&tmu[i], a.mu + q, ok);
+    // K and mu halo tiles arrive by 16-byte cp.async: rows z0-H .. z0+TZ+H-1, columns
+    // x0-4 .. x0+TX+3 (x0-4 is 16-byte aligned: the row pitch is a multiple of 32
+    // elements).  Rows past nz+H-1 and chunks that would end past the allocation are
+    // zero-filled; columns past nx+H-1 feed no stored point ...
+    for (int i = tid; i < (TZ + 2 * H) * CHR; i += 256) {
+        const int r = i / CHR, c = i - r * CHR;
+        const int64_t z = z0 - H + r;
+        const int64_t q = (z + H + 1) * L.px + x0 - 4 + V * c;
+        const bool ok = z < L.nz + H && q + V <= L.total;
+        cp_async<16>(&tile[r][V * c], ok ? a.Kh + q : a.Kh, ok);
+        cp_async<16>(&tmu[r * W + V * c], ok ? a.mu + q : a.mu, ok);
     }
     cp_async_commit();
     for (int i = tid; i < TZ * TX; i += 256) sw[i] = (T)0;
@@ -1232,12 +1237,12 @@ __device__ __forceinline__ void adj2d_tile(const AdjArgs<T>& a, int64_t bx, int6
     __syncthreads();
     for (int i = tid; i < TZ * TX; i += 256) {
         int lz = i / TX, lx = i - lz * TX;
-        T c = tile[lz + H][lx + H];
+        T c = tile[lz + H][lx + 4];
         T s = 0;
 #pragma unroll
         for (int k = 1; k <= H; ++k)
-            s += a.w2[k] * (((tile[lz + H][lx + H + k] - c) + (tile[lz + H][lx + H - k] - c)) +
-                            ((tile[lz + H + k][lx + H] - c) + (tile[lz + H - k][lx + H] - c)));
+            s += a.w2[k] * (((tile[lz + H][lx + 4 + k] - c) + (tile[lz + H][lx + 4 - k] - c)) +
+                            ((tile[lz + H + k][lx + 4] - c) + (tile[lz + H - k][lx + 4] - c)));
         acc[i] = s;
     }
     tile_sources<T, TX, TZ>(a.src, (T)1, origin, L.px, sw, tid);
@@ -1292,8 +1297,8 @@ __device__ __forceinline__ void adj2d_tile(const AdjArgs<T>& a, int64_t bx, int6
 
 template <typename T, int H, int TX, int TZ>
 __global__ void __launch_bounds__(256) k_adj2d(AdjArgs<T> a) {
-    __shared__ T tile[TZ + 2 * H][TX + 2 * H];     // K mu on the halo tile
-    __shared__ T tmu[(TZ + 2 * H) * (TX + 2 * H)];
+    __shared__ __align__(16) T tile[TZ + 2 * H][TX + 8];     // K mu on the halo tile
+    __shared__ __align__(16) T tmu[(TZ + 2 * H) * (TX + 8)];
     __shared__ T acc[TZ * TX];
     __shared__ T sw[TZ * TX];                      // source weights landing in the tile
     adj2d_tile<T, H, TX, TZ>(a, blockIdx.x, blockIdx.y, tile, tmu, acc, sw);
@@ -1311,11 +1316,11 @@ struct AdjBatch {
 };
 
 template <typename T, int H, int TX, int TZ>
-__global__ void __launch_bounds__(256) k_adj2d_batch(const AdjBatch<T>* __restrict__ shots,
+__global__ void __launch_bounds__(256, 3) k_adj2d_batch(const AdjBatch<T>* __restrict__ shots,
                                                      const int64_t* __restrict__ tile0,
                                                      const int32_t* __restrict__ shot_of, int m, int j, int nt) {
-    __shared__ T tile[TZ + 2 * H][TX + 2 * H];
-    __shared__ T tmu[(TZ + 2 * H) * (TX + 2 * H)];
+    __shared__ __align__(16) T tile[TZ + 2 * H][TX + 8];
+    __shared__ __align__(16) T tmu[(TZ + 2 * H) * (TX + 8)];
     __shared__ T acc[TZ * TX];
     __shared__ T sw[TZ * TX];
     const int64_t b = blockIdx.x;
