@@ -199,9 +199,12 @@ ib_status ib_adjoint(const ib_table* table, const ib_shot* shot, int32_t precisi
 /*
  * ib_forward_batch -- many independent shots, each with its own table (grid
  * and topography), advanced together: every time step is one launch that
- * covers the tiles of all shots.  Same semantics per shot as ib_forward
- * (precision 32, no checkpoints).  tables[i] and shots[i] are host arrays of
- * length nshot.
+ * covers the tiles (or z-marched strips of tiles) of all shots, and all steps
+ * are one captured CUDA graph.  The tile shape is timed on the first batch of
+ * a size class and remembered; the environment variable IB_BATCH_SHAPE=<0..7>
+ * fixes it instead (IB_ERR_ARG outside that range).  Same semantics per shot
+ * as ib_forward (precision 32, no checkpoints).  tables[i] and shots[i] are
+ * host arrays of length nshot.
  */
 ib_status ib_forward_batch(const ib_table* const* tables, const ib_shot* shots,
                            int32_t nshot, int32_t precision, double dt, int32_t nt,
