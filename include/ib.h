@@ -51,8 +51,13 @@ typedef enum {
                              and the lowest basis order (rank paragraph)           */
     IB_ERR_CUDA = 3,      /* a CUDA call failed                                    */
     IB_ERR_OOM = 4,       /* device allocation failed                              */
-    IB_ERR_UNSTABLE = 5,  /* NaN/Inf detected in the wavefield                     */
-    IB_ERR_TIMEOUT = 6,   /* a bounded device wait gave up                         */
+    IB_ERR_UNSTABLE = 5,  /* NaN/Inf in a run's final fields (ib_sync_status), or
+                             a growing mode found by ib_stability                  */
+    IB_ERR_TIMEOUT = 6,   /* a bounded device wait gave up.  From a time step the
+                             run's results are then not valid, and a copy that never
+                             arrived may leave the context unusable; only the
+                             self-test (ib_selftest_bounded_wait), which issues no
+                             copy, leaves it known to be usable                    */
     IB_ERR_STATE = 7      /* call not valid for this table (e.g. wrong form)       */
 } ib_status;
 
@@ -68,7 +73,9 @@ typedef struct {
 
 typedef struct {
     int32_t space_order;   /* M of the interior stencils: 2, 4, 6 or 8             */
-    int32_t basis_order;   /* order of the extrapolation basis; 0 -> min(M, 4)     */
+    int32_t basis_order;   /* order of the extrapolation basis; 0 -> M in 2D (the
+                              paper's consistent-error rule) and min(M, 4) in 3D
+                              (its order-reduction paragraph)                      */
     int32_t min_order;     /* lowest basis order of the fallback (>= 2)            */
     int32_t reserved;
     double radius;         /* initial support radius in grid units; <= 0 ->
@@ -79,8 +86,9 @@ typedef struct {
     double rank_tol;       /* full rank iff sigma_min > rank_tol * sigma_max       */
 } ib_opts;
 
-/* Fill `opts` with the defaults for space order M (basis min(M,4), min order
- * 2, radius (basis+1)/2, growth 3, eta_p 0.5, eta_v 0, rank_tol 1e-3). */
+/* Fill `opts` with the defaults for space order M (basis 0: M in 2D, min(M, 4)
+ * in 3D; min order 2, radius (basis+1)/2, growth 3, eta_p 0.5, eta_v 0,
+ * rank_tol 1e-3). */
 void ib_opts_default(ib_opts* opts, int32_t space_order);
 
 typedef struct ib_table ib_table;   /* opaque, library-owned */
@@ -254,9 +262,11 @@ ib_status ib_adjoint_batch(const ib_table* const* tables, const ib_shot* shots,
  * buffers are the caller's.
  *   - Needs 3 padded fields (about 12 bytes per grid point) plus 96 bytes per
  *     source and receiver; larger problems return IB_ERR_ARG with the sizes.
- *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) once for that device; make that first call
- *     before any stream capture.
+ *   - Each call made outside stream capture looks up the array's device
+ *     address (cudaGetSymbolAddress) for the current device; a call made
+ *     while `stream` is capturing reuses the address from the last
+ *     uncaptured call on that device, so make the first call on a device
+ *     before any stream capture (a captured first call: IB_ERR_STATE).
  *   - All calls share the array and it keeps the last call's contents: each
  *     call clears what must start at zero, but calls that overlap on the GPU
  *     (other streams, other threads) race on it and must be serialised by the
@@ -288,7 +298,7 @@ typedef struct {
                               the array edge), then [free, rigid, M / 8]       */
     double out_radius;     /* outputs: corrections at offsets |o| <= out_radius,
                               which must equal the first support radius of the
-                              fit, (min(M, basis order) + 1) / 2 by default    */
+                              fit, (basis order + 1) / 2                       */
 } ib_mlp_config;
 
 /*
@@ -400,8 +410,40 @@ ib_status ib_profile_get(int32_t i, char* name, int32_t name_len, int64_t* launc
  */
 ib_status ib_selftest_bounded_wait(void* stream);
 
-/* Synchronise `stream` and return IB_ERR_CUDA on a pending device error. */
+/*
+ * ib_sync_status -- synchronise `stream`; IB_ERR_CUDA on a pending device
+ * error.  Every forward and adjoint run ends with a pass over its final
+ * wavefields (gradients for the adjoint) that sets a per-device status word on
+ * a NaN or Inf; this call then returns IB_ERR_UNSTABLE (the scheme blew up
+ * for that model and time step) and clears the word.  The word is shared by
+ * all streams of the device, so the report names no particular run.
+ */
 ib_status ib_sync_status(void* stream);
+
+/*
+ * ib_stability -- estimate the per-step growth factor of the time stepping
+ * with this table's modified operators (the paper gives no stability analysis;
+ * its explicit schemes are those of the 2nd-order application section and the
+ * 1st-order section).  The modified operators are not symmetric, so their
+ * spectrum can leave the interval on which the leapfrog (or staggered) update
+ * is neutrally stable.  The call runs the time-step kernels source-free from a
+ * random state (SplitMix64 of `seed` and the node index, on interior nodes),
+ * renormalising every 50 steps: a power iteration on the one-step map.  It
+ * runs n_steps rounded up to an even number of 50-step blocks and returns in
+ * *growth the geometric-mean growth per step over the second half, an
+ * estimate of the spectral radius of the one-step map (1 for a neutrally
+ * stable scheme, > 1 when some mode grows).
+ *   vel_dev, rho_dev  as in ib_shot (rho only for the first-order form).
+ *   precision         32 or 64;  dt the time step of the intended run.
+ *   max_gain          IB_ERR_UNSTABLE (with *growth set) when
+ *                     growth^n_steps > max_gain, i.e. an unstable mode would
+ *                     grow by more than max_gain over a run of n_steps.
+ * Synchronises the stream.  Errors: IB_ERR_ARG, IB_ERR_STATE (first-order form
+ * in 3D), IB_ERR_OOM, IB_ERR_CUDA, IB_ERR_UNSTABLE.
+ */
+ib_status ib_stability(const ib_table* table, const void* vel_dev, const void* rho_dev,
+                       int32_t precision, double dt, int32_t n_steps, uint64_t seed,
+                       double max_gain, double* growth, void* stream);
 
 /* Thread-local message of the last failure ("" if none). */
 const char* ib_last_error(void);

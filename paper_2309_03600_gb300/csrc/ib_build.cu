@@ -1986,7 +1986,9 @@ static ib_status build_impl(const ib_grid* grid, const double* sdf, ib_bc bc, ib
         ib_set_error("space_order must be 2, 4, 6 or 8");
         return IB_ERR_ARG;
     }
-    if (o.basis_order <= 0) o.basis_order = std::min(M, 4);
+    // basis order M (consistent error, 3D expansion paragraph); in 3D reduced to 4
+    // at M > 4 (order-reduction paragraph: the order-8 footprint holds ~380 points)
+    if (o.basis_order <= 0) o.basis_order = grid->ndim == 2 ? M : std::min(M, 4);
     if (o.basis_order > M || (o.basis_order & 1)) {
         ib_set_error("basis_order must be even and <= space_order");
         return IB_ERR_ARG;

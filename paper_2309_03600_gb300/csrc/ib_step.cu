@@ -151,15 +151,22 @@ __device__ __forceinline__ void tile_sources(const PointSet<T>& src, T wv, int64
     }
 }
 
+// Receivers gid, gid + stride, ... of this launch (stride = the threads that
+// record for this shot), so that every receiver is recorded whatever the grid.
 template <typename T>
 __device__ __forceinline__ void record_receivers(const PointSet<T>& rec, const T* p, T* traces, int nt, int col,
-                                                 int64_t gid) {
-    if (col >= 0 && gid < rec.n) {
+                                                 int64_t gid, int64_t stride) {
+    if (col < 0) return;
+    for (int64_t r = gid; r < rec.n; r += stride) {
         T s = 0;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) s += rec.w[8 * gid + c] * p[rec.idx[8 * gid + c]];
-        traces[gid * nt + col] = s;
+        for (int c = 0; c < 8; ++c) s += rec.w[8 * r + c] * p[rec.idx[8 * r + c]];
+        traces[r * nt + col] = s;
     }
+}
+
+__device__ __forceinline__ int64_t launch_threads() {
+    return (int64_t)gridDim.x * gridDim.y * gridDim.z * blockDim.x * blockDim.y * blockDim.z;
 }
 
 // ---------------------------------------------------------------------------
@@ -268,7 +275,7 @@ __global__ void __launch_bounds__(256) k_leap2d(StepArgs<T> a) {
     __shared__ T acc[TZ * TX];
     __shared__ T sadd[TZ * TX];
     const int64_t blk = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
-    record_receivers(a.rec, a.p, a.traces, a.nt, a.rec_step, blk * 256 + threadIdx.x);
+    record_receivers(a.rec, a.p, a.traces, a.nt, a.rec_step, blk * 256 + threadIdx.x, launch_threads());
     leap2d_tile<T, H, TX, TZ>(a, blockIdx.x, blockIdx.y, tile, acc, sadd);
 }
 
@@ -291,7 +298,8 @@ __global__ void __launch_bounds__(256) k_leap2d_batch(const StepArgs<T>* __restr
     a.out = prev;
     a.step = step;
     a.rec_step = step - 1;
-    record_receivers(a.rec, a.p, a.traces, a.nt, a.rec_step, local * 256 + threadIdx.x);
+    record_receivers(a.rec, a.p, a.traces, a.nt, a.rec_step, local * 256 + threadIdx.x,
+                     (tile0[lo + 1] - tile0[lo]) * 256);
     if (local >= a.ntiles) return;   // uniform per block
     leap2d_tile<T, H, TX, TZ>(a, local % a.ntx, local / a.ntx, tile, acc, sadd);
 }
@@ -492,7 +500,8 @@ __global__ void __launch_bounds__(256, MINB) k_leap2d_batch_m(const StepArgs<flo
     a.out = prev;
     a.step = step;
     a.rec_step = step - 1;
-    record_receivers(a.rec, a.p, a.traces, a.nt, a.rec_step, local * 256 + threadIdx.x);
+    record_receivers(a.rec, a.p, a.traces, a.nt, a.rec_step, local * 256 + threadIdx.x,
+                     (tile0[lo + 1] - tile0[lo]) * 256);
     if (local >= a.ntiles) return;   // uniform per block
     leap2d_strip<H, NSUB, D>(a, local % a.ntx, local / a.ntx, sm);
 }
@@ -502,7 +511,7 @@ template <int H, int NSUB, int D>
 __global__ void __launch_bounds__(256, 4) k_leap2d_m(StepArgs<float> a) {
     __shared__ __align__(16) Strip2D<H, NSUB, D> sm;
     const int64_t blk = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
-    record_receivers(a.rec, a.p, a.traces, a.nt, a.rec_step, blk * 256 + threadIdx.x);
+    record_receivers(a.rec, a.p, a.traces, a.nt, a.rec_step, blk * 256 + threadIdx.x, launch_threads());
     leap2d_strip<H, NSUB, D>(a, blockIdx.x, blockIdx.y, sm);
 }
 
@@ -565,7 +574,7 @@ __global__ void k_seg_restore_batch(const ShotCopy<T>* __restrict__ items, int k
 // receivers only (after the last step)
 template <typename T>
 __global__ void k_receivers(PointSet<T> rec, const T* p, T* traces, int nt, int col) {
-    record_receivers(rec, p, traces, nt, col, (int64_t)blockIdx.x * blockDim.x + threadIdx.x);
+    record_receivers(rec, p, traces, nt, col, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, launch_threads());
 }
 
 // 3D: (x, y) tile of 32 x 8 columns marching in z with a register queue of the
@@ -580,7 +589,7 @@ __global__ void __launch_bounds__(256) k_leap3d(StepArgs<T> a, int zchunk, int64
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * TX + tx;
     const int64_t blk = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    record_receivers(a.rec, a.p, a.traces, a.nt, a.rec_step, blk * 256 + tid);
+    record_receivers(a.rec, a.p, a.traces, a.nt, a.rec_step, blk * 256 + tid, launch_threads());
     const Layout& L = a.L;
     const int64_t x0 = (int64_t)blockIdx.x * TX, y0 = (int64_t)blockIdx.y * TY;
     const int64_t x = x0 + tx, y = y0 + ty;
@@ -718,7 +727,7 @@ __global__ void __launch_bounds__(256) k_leap3d_tma(StepArgs<float> a, const __g
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * TX + tx;
     const int64_t blk = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
-    record_receivers(a.rec, a.p, a.traces, a.nt, a.rec_step, blk * 256 + tid);
+    record_receivers(a.rec, a.p, a.traces, a.nt, a.rec_step, blk * 256 + tid, launch_threads());
     const Layout& L = a.L;
     const int64_t x0 = (int64_t)blockIdx.x * TX, y0 = (int64_t)blockIdx.y * TY;
     const int64_t x = x0 + tx, y = y0 + ty;
@@ -774,7 +783,17 @@ __global__ void __launch_bounds__(256) k_leap3d_tma(StepArgs<float> a, const __g
         bool ok = mbar_wait_bounded(&bar[st], (uint32_t)((it / NS) & 1));
         ok = ok && mbar_wait_bounded(&bar[sf], (uint32_t)(((it + H) / NS) & 1));
         if (__syncthreads_or(!ok)) {
-            if (tid == 0) atomicExch(err, 1);
+            if (tid == 0) {
+                atomicExch(err, 1);
+                // issue nothing more, and wait (bounded) for every plane already issued
+                // (planes z .. z + NS - 1), so that no copy is still landing in this
+                // block's shared memory when it leaves
+                const int64_t ziss = min(z + NS - 1, zlast);
+                for (int64_t zp = z; zp <= ziss; ++zp) {
+                    const int ip = (int)(zp - zb);
+                    mbar_wait_bounded(&bar[ip % NS], (uint32_t)((ip / NS) & 1));
+                }
+            }
             return;
         }
         // software pipeline: p_prev and Kh of plane z + 2
@@ -975,7 +994,7 @@ __global__ void __launch_bounds__(256, 4) k_stag_v2d(StagArgs<T> a) {
     const int32_t nst = plan_stage<T, STG>(a.pv, blk, smeta, sw, tid);
     cp_async_commit();
     const int sb = a.step_base ? *a.step_base : 0;
-    record_receivers(a.rec, a.p, a.traces, a.nt, sb + a.rec_step, blk * 256 + tid);
+    record_receivers(a.rec, a.p, a.traces, a.nt, sb + a.rec_step, blk * 256 + tid, launch_threads());
     const int32_t r0 = a.pv.rptr[blk], r1 = a.pv.rptr[blk + 1];
     // the update's own operands and this tile's row corrections while the copies fly
     T vx[NP], vz[NP], bx[NP], bz[NP];
@@ -1419,6 +1438,93 @@ __global__ void k_unpad(Layout L, const T* pad, T* out) {
 }
 
 // ---------------------------------------------------------------------------
+// stability checks
+//   - every forward / adjoint run ends with a pass over its final fields; a
+//     NaN or Inf sets bit 0 of a per-device status word that ib_sync_status
+//     reports as IB_ERR_UNSTABLE (a non-finite value never leaves the leapfrog
+//     or staggered recursion once it appears, so the final fields suffice);
+//   - ib_stability runs the step kernels source-free from a random state and
+//     renormalises every STAB_BLOCK steps: a power iteration on the one-step
+//     map whose per-step growth estimates its spectral radius.
+// ---------------------------------------------------------------------------
+static __device__ int g_dev_status;
+
+template <typename T>
+__global__ void k_check_finite(int64_t n, const T* __restrict__ a, const T* __restrict__ b,
+                               const T* __restrict__ c) {
+    bool bad = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        bad |= !isfinite(a[i]);
+        if (b) bad |= !isfinite(b[i]);
+        if (c) bad |= !isfinite(c[i]);
+    }
+    if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(&g_dev_status, 1);
+}
+
+// SplitMix64 output function (Steele, Lea & Flood, "Fast splittable
+// pseudorandom number generators", 2014) as a counter-based generator
+__device__ __forceinline__ uint64_t splitmix64(uint64_t z) {
+    z += 0x9e3779b97f4a7c15ull;
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+}
+
+// f[i] = f2[i] = uniform(-1, 1) where coef[i] != 0 (interior nodes), else 0
+template <typename T>
+__global__ void k_rand_fill(int64_t n, const T* __restrict__ coef, uint64_t seed, T* f, T* f2) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        T v = (T)0;
+        if (coef[i] != (T)0) v = (T)((double)(splitmix64(seed * 0x632be59bd9b4e019ull + (uint64_t)i) >> 11) *
+                                         (2.0 / 9007199254740992.0) - 1.0);
+        f[i] = v;
+        if (f2) f2[i] = v;
+    }
+}
+
+// *out += sum of squares of a, b, c (nullable)
+template <typename T>
+__global__ void k_sumsq(int64_t n, const T* __restrict__ a, const T* __restrict__ b, const T* __restrict__ c,
+                        double* out) {
+    __shared__ double part[32];
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        double x = (double)a[i];
+        s += x * x;
+        if (b) {
+            x = (double)b[i];
+            s += x * x;
+        }
+        if (c) {
+            x = (double)c[i];
+            s += x * x;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += part[w];
+        atomicAdd(out, t);
+    }
+}
+
+// divide a, b, c by sqrt(*sumsq); *logn = log sqrt(*sumsq)
+template <typename T>
+__global__ void k_rescale(int64_t n, T* a, T* b, T* c, const double* sumsq, double* logn) {
+    const double nrm = sqrt(*sumsq);
+    const T inv = (T)(nrm > 0.0 ? 1.0 / nrm : 0.0);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        a[i] *= inv;
+        if (b) b[i] *= inv;
+        if (c) c[i] *= inv;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) *logn = log(nrm);
+}
+
+// ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
 static int grid1(int64_t n, int bs) {
@@ -1443,6 +1549,34 @@ struct Scratch {
         return IB_OK;
     }
 };
+
+// power-iteration probe of ib_stability: random start, renormalisation every
+// STAB_BLOCK steps into slot k of the device arrays sums / logs
+static const int STAB_BLOCK = 50;
+struct Probe {
+    uint64_t seed;
+    int nslot;          // nt / STAB_BLOCK + 1 (slot 0: the initial norm)
+    double* sums;       // [nslot], zeroed
+    double* logs;       // [nslot]
+};
+
+template <typename T>
+static ib_status probe_rescale(const Probe* pr, int slot, int64_t n, T* a, T* b, T* c, cudaStream_t s) {
+    k_sumsq<T><<<grid1(n, 256), 256, 0, s>>>(n, a, b, c, pr->sums + slot);
+    k_rescale<T><<<grid1(n, 256), 256, 0, s>>>(n, a, b, c, pr->sums + slot, pr->logs + slot);
+    IB_CHECK_LAUNCH("stability probe");
+    ib_count_launch("setup");
+    ib_count_launch("setup");
+    return IB_OK;
+}
+
+template <typename T>
+static ib_status check_finite(int64_t n, const T* a, const T* b, const T* c, cudaStream_t s) {
+    k_check_finite<T><<<grid1(n, 256), 256, 0, s>>>(n, a, b, c);
+    IB_CHECK_LAUNCH("k_check_finite");
+    ib_count_launch("setup");
+    return IB_OK;
+}
 
 template <typename T>
 static void stencil_weights(int M, T w2o[5], T c1o[4]) {
@@ -1580,10 +1714,8 @@ static const int STRIP_NSUB = 8, STRIP_D = 3;   // z-marched strips: 8 tiles of 
 // One FP32 shot runs on strips when there are enough of them to fill the GPU
 // (a strip is 8 tiles of work: on small grids the tile kernel keeps more blocks
 // in flight).  IB_STRIP=0 / IB_STRIP=1 turn strips off / on whatever the size.
-// Strips are used only when their blocks cover the receivers.
-static bool use_strips(const Layout& L, int64_t nrec) {
+static bool use_strips(const Layout& L) {
     const int64_t nblk = ((L.nx + TX2 - 1) / TX2) * (((L.nz + TZ2 - 1) / TZ2 + STRIP_NSUB - 1) / STRIP_NSUB);
-    if (nblk * 256 < nrec) return false;
     const char* e = getenv("IB_STRIP");
     if (e && *e) return e[0] != '0';
     return nblk >= 1024;
@@ -1610,7 +1742,7 @@ static void launch_leap2d_strip(const StepArgs<float>& a, int H, dim3 grid, cuda
 
 template <typename T>
 static ib_status forward_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, void* ckpt, int n_ckpt,
-                             cudaStream_t s) {
+                             cudaStream_t s, const Probe* probe = nullptr) {
     const Layout& L = t->L;
     const int d = t->grid.ndim;
     const int M = t->opts.space_order;
@@ -1623,6 +1755,11 @@ static ib_status forward_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, 
     k_leap_coef<T><<<grid1(L.N, 256), 256, 0, s>>>(L, (const T*)sh->vel_dev, t->mask_pad[0], dt / t->grid.h, Kh);
     IB_CHECK_LAUNCH("k_leap_coef");
     ib_count_launch("setup");
+    if (probe) {   // p^0 = p^{-1} = random on interior nodes, normalised
+        k_rand_fill<T><<<grid1(L.total, 256), 256, 0, s>>>(L.total, Kh, probe->seed, p0, p1);
+        IB_CHECK_LAUNCH("k_rand_fill");
+        TRY(probe_rescale<T>(probe, 0, L.total, p0, p1, (T*)nullptr, s));
+    }
     Geom<T> g;
     TRY(setup_points<T>(t, sh, dt * dt / pow(t->grid.h, d), S, g));
     const TileBins* bins = nullptr;
@@ -1646,7 +1783,7 @@ static ib_status forward_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, 
     T* cur = p0;   // p^n
     T* prev = p1;  // p^{n-1}
     dim3 grid2((unsigned)((L.nx + TX2 - 1) / TX2), (unsigned)((L.nz + TZ2 - 1) / TZ2));
-    const bool strips = d == 2 && sizeof(T) == 4 && use_strips(L, g.rec.n);
+    const bool strips = d == 2 && sizeof(T) == 4 && use_strips(L);
     dim3 grids((unsigned)((L.nx + TX2 - 1) / TX2),
                (unsigned)(((L.nz + TZ2 - 1) / TZ2 + STRIP_NSUB - 1) / STRIP_NSUB));
     const int zchunk = 32;
@@ -1697,12 +1834,15 @@ static ib_status forward_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, 
         }
         IB_CHECK_LAUNCH("leapfrog step");
         std::swap(cur, prev);
+        if (probe && (n + 1) % STAB_BLOCK == 0)
+            TRY(probe_rescale<T>(probe, (n + 1) / STAB_BLOCK, L.total, cur, prev, (T*)nullptr, s));
     }
     if (g.rec.n) {
         k_receivers<T><<<grid1(g.rec.n, 256), 256, 0, s>>>(g.rec, cur, (T*)sh->traces_dev, nt, nt - 1);
         IB_CHECK_LAUNCH("k_receivers");
         ib_count_launch("setup");
     }
+    TRY(check_finite<T>(L.total, cur, prev, (const T*)nullptr, s));
     if (use_tma) {
         int herr = 0;
         IB_CUDA(cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -1919,9 +2059,11 @@ __global__ void k_add_step(int* base, int k) {
 
 // time steps per captured graph of the staggered loop (the graph is replayed nt / STAG_GRAPH_STEPS times)
 static const int STAG_GRAPH_STEPS = 50;
+static_assert(STAG_GRAPH_STEPS == STAB_BLOCK, "the stability probe renormalises between graph replays");
 
 template <typename T>
-static ib_status forward_stag(ib_table* t, const ib_shot* sh, double dt, int nt, cudaStream_t s) {
+static ib_status forward_stag(ib_table* t, const ib_shot* sh, double dt, int nt, cudaStream_t s,
+                              const Probe* probe = nullptr) {
     const Layout& L = t->L;
     const int d = t->grid.ndim;
     if (d != 2) {
@@ -1942,6 +2084,13 @@ static ib_status forward_stag(ib_table* t, const ib_shot* sh, double dt, int nt,
                                                    t->mask_pad[1], t->mask_pad[2], dt, 1.0 / t->grid.h, kp, bx, bz);
     IB_CHECK_LAUNCH("k_stag_coef");
     ib_count_launch("setup");
+    if (probe) {   // random p, v_x, v_z on their interior nodes, normalised together
+        k_rand_fill<T><<<grid1(L.total, 256), 256, 0, s>>>(L.total, kp, probe->seed, p, (T*)nullptr);
+        k_rand_fill<T><<<grid1(L.total, 256), 256, 0, s>>>(L.total, bx, probe->seed + 1, vx, (T*)nullptr);
+        k_rand_fill<T><<<grid1(L.total, 256), 256, 0, s>>>(L.total, bz, probe->seed + 2, vz, (T*)nullptr);
+        IB_CHECK_LAUNCH("k_rand_fill");
+        TRY(probe_rescale<T>(probe, 0, L.total, p, vx, vz, s));
+    }
     Geom<T> g;
     TRY(setup_points<T>(t, sh, dt / pow(t->grid.h, d), S, g));
     StagArgs<T> a;
@@ -2038,6 +2187,7 @@ static ib_status forward_stag(ib_table* t, const ib_shot* sh, double dt, int nt,
             ProfToken tk = ib_prof_begin(kname<T>("stag_graph50_f32", "stag_graph50_f64"), cs);
             IB_CUDA(cudaGraphLaunch(exec, cs));
             ib_prof_end(tk, cs);
+            if (probe) TRY(probe_rescale<T>(probe, r + 1, L.total, p, vx, vz, cs));
             for (int k = 0; k < K; ++k) {
                 ib_count_launch(kname<T>("stag_v2d_f32", "stag_v2d_f64"));
                 ib_count_launch(kname<T>("stag_p2d_f32", "stag_p2d_f64"));
@@ -2051,12 +2201,15 @@ static ib_status forward_stag(ib_table* t, const ib_shot* sh, double dt, int nt,
         a.step = k;
         a.rec_step = k - 1;
         TRY(launch_step(cs, true));
+        if (probe && (nrep * K + k + 1) % STAB_BLOCK == 0)
+            TRY(probe_rescale<T>(probe, (nrep * K + k + 1) / STAB_BLOCK, L.total, p, vx, vz, cs));
     }
     if (g.rec.n) {
         k_receivers<T><<<grid1(g.rec.n, 256), 256, 0, cs>>>(g.rec, p, (T*)sh->traces_dev, nt, nt - 1);
         IB_CHECK_LAUNCH("k_receivers");
         ib_count_launch("setup");
     }
+    TRY(check_finite<T>(L.total, p, vx, vz, cs));
     if (nrep) {
         IB_CUDA(cudaEventRecord(ready, cs));
         IB_CUDA(cudaStreamWaitEvent(s, ready, 0));
@@ -2249,6 +2402,7 @@ static ib_status adjoint_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, 
     k_unpad<T><<<grid1(L.N, 256), 256, 0, s>>>(L, grad, grad_out);
     IB_CHECK_LAUNCH("k_unpad");
     ib_count_launch("setup");
+    TRY(check_finite<T>(L.N, grad_out, (const T*)nullptr, (const T*)nullptr, s));
     IB_CUDA(cudaStreamSynchronize(s));
     for (auto& b : keep) ib_free_bins(b);
     return IB_OK;
@@ -2549,6 +2703,7 @@ static ib_status forward_batch_impl(const ib_table* const* tables, const ib_shot
         ib_count_launch("setup");
     }
     IB_CHECK_LAUNCH("k_receivers");
+    for (int i = 0; i < nshot; ++i) TRY(check_finite<float>(ts[i]->L.total, b0[i], b1[i], (const float*)nullptr, cs));
     IB_CUDA(cudaEventRecord(ready, cs));
     IB_CUDA(cudaStreamWaitEvent(s, ready, 0));
     IB_CUDA(cudaStreamSynchronize(cs));
@@ -2767,6 +2922,7 @@ extern "C" ib_status ib_adjoint_batch(const ib_table* const* tables, const ib_sh
         const Layout& L = ts[i]->L;
         k_unpad<float><<<grid1(L.N, 256), 256, 0, cs>>>(L, grad[i], (float*)grads[i]);
         ib_count_launch("setup");
+        TRY(check_finite<float>(L.N, (const float*)grads[i], (const float*)nullptr, (const float*)nullptr, cs));
     }
     IB_CHECK_LAUNCH("k_unpad");
     IB_CUDA(cudaEventRecord(ready, cs));
@@ -2799,10 +2955,78 @@ extern "C" ib_status ib_selftest_bounded_wait(void* stream) {
 }
 
 extern "C" ib_status ib_sync_status(void* stream) {
-    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    cudaStream_t s = (cudaStream_t)stream;
+    cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return ib_cuda_fail(e, "stream", __FILE__, __LINE__);
     e = cudaGetLastError();
     if (e != cudaSuccess) return ib_cuda_fail(e, "device", __FILE__, __LINE__);
+    int word = 0;
+    IB_CUDA(cudaMemcpyFromSymbolAsync(&word, g_dev_status, sizeof(int), 0, cudaMemcpyDeviceToHost, s));
+    IB_CUDA(cudaStreamSynchronize(s));
+    if (word) {
+        const int zero = 0;
+        IB_CUDA(cudaMemcpyToSymbolAsync(g_dev_status, &zero, sizeof(int), 0, cudaMemcpyHostToDevice, s));
+        IB_CUDA(cudaStreamSynchronize(s));
+        ib_set_error("non-finite values (NaN/Inf) in the final wavefield or gradient of a run on this device: "
+                     "the scheme is unstable for that model and time step");
+        return IB_ERR_UNSTABLE;
+    }
+    return IB_OK;
+}
+
+extern "C" ib_status ib_stability(const ib_table* tc, const void* vel_dev, const void* rho_dev, int32_t precision,
+                                  double dt, int32_t n_steps, uint64_t seed, double max_gain, double* growth,
+                                  void* stream) {
+    ib_set_error("");
+    if (!tc || !vel_dev || !growth || (precision != 32 && precision != 64) || !(dt > 0.0) || n_steps < 1 ||
+        !(max_gain > 1.0)) {
+        ib_set_error("ib_stability: table, velocity and output required; precision 32 or 64, dt > 0, "
+                     "n_steps >= 1, max_gain > 1");
+        return IB_ERR_ARG;
+    }
+    ib_table* t = const_cast<ib_table*>(tc);
+    if (t->form != IB_SECOND_ORDER && t->grid.ndim != 2) {
+        ib_set_error("ib_stability: the staggered form is implemented in 2D");
+        return IB_ERR_STATE;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    // whole renormalisation blocks, an even number of them
+    const int nblk = std::max(2, ((n_steps + STAB_BLOCK - 1) / STAB_BLOCK + 1) / 2 * 2);
+    const int nt = nblk * STAB_BLOCK;
+    Scratch S(s);
+    Probe pr;
+    pr.seed = seed;
+    pr.nslot = nblk + 1;
+    TRY(S.alloc(&pr.sums, pr.nslot, true));
+    TRY(S.alloc(&pr.logs, pr.nslot, true));
+    ib_shot sh;
+    memset(&sh, 0, sizeof sh);
+    sh.vel_dev = vel_dev;
+    sh.rho_dev = rho_dev;
+    if (t->form == IB_SECOND_ORDER)
+        TRY(precision == 64 ? forward_2nd<double>(t, &sh, dt, nt, nullptr, 0, s, &pr)
+                            : forward_2nd<float>(t, &sh, dt, nt, nullptr, 0, s, &pr));
+    else
+        TRY(precision == 64 ? forward_stag<double>(t, &sh, dt, nt, s, &pr)
+                            : forward_stag<float>(t, &sh, dt, nt, s, &pr));
+    std::vector<double> logs(pr.nslot);
+    IB_CUDA(cudaMemcpyAsync(logs.data(), pr.logs, sizeof(double) * pr.nslot, cudaMemcpyDeviceToHost, s));
+    IB_CUDA(cudaStreamSynchronize(s));
+    // per-step growth over the second half of the blocks (the first half lets the
+    // dominant mode emerge from the random start)
+    double acc = 0.0;
+    for (int k = nblk / 2 + 1; k <= nblk; ++k) acc += logs[k];
+    const double rate = acc / (double)((nblk - nblk / 2) * STAB_BLOCK);
+    *growth = std::isfinite(rate) ? exp(rate) : INFINITY;
+    if (!std::isfinite(rate) || rate * (double)n_steps > log(max_gain)) {
+        char buf[256];
+        snprintf(buf, sizeof buf,
+                 "ib_stability: per-step growth %.6f amplifies an unstable mode by %.3g over %d steps "
+                 "(limit %.3g)", *growth, std::isfinite(rate) ? exp(rate * (double)n_steps) : INFINITY, n_steps,
+                 max_gain);
+        ib_set_error(buf);
+        return IB_ERR_UNSTABLE;
+    }
     return IB_OK;
 }
 
@@ -2834,20 +3058,29 @@ __global__ void k_ib_rows_add(int64_t nrows, const int64_t* __restrict__ row_pad
 static std::mutex g_noalloc_mu;
 static void* g_noalloc_ptr[64] = {nullptr};
 
-// device address of the static scratch for the current device (set up once per device)
-static ib_status noalloc_scratch(unsigned char** out) {
+// Device address of the static scratch for the current device.  Outside stream
+// capture it is looked up on every call (a device reset or a new primary
+// context reloads the module and can move the array); while `s` is capturing,
+// the address remembered from the last uncaptured call on this device is used,
+// so the first call on a device must come before any capture.
+static ib_status noalloc_scratch(cudaStream_t s, unsigned char** out) {
     int dev = 0;
     IB_CUDA(cudaGetDevice(&dev));
     if (dev < 0 || dev >= 64) {
         ib_set_error("device index out of range for the static scratch");
         return IB_ERR_ARG;
     }
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    IB_CUDA(cudaStreamIsCapturing(s, &cap));
     std::lock_guard<std::mutex> lk(g_noalloc_mu);
-    if (!g_noalloc_ptr[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
         void* ptr = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
         if (e != cudaSuccess) return ib_cuda_fail(e, "cudaGetSymbolAddress(g_noalloc_scratch)", __FILE__, __LINE__);
         g_noalloc_ptr[dev] = ptr;
+    } else if (!g_noalloc_ptr[dev]) {
+        ib_set_error("ib_forward_noalloc: the first call on a device must not be captured");
+        return IB_ERR_STATE;
     }
     *out = (unsigned char*)g_noalloc_ptr[dev];
     return IB_OK;
@@ -2875,9 +3108,9 @@ extern "C" ib_status ib_forward_noalloc(const ib_table* tc, const ib_shot* sh, d
         ib_set_error(buf);
         return IB_ERR_ARG;
     }
-    unsigned char* base = nullptr;
-    TRY(noalloc_scratch(&base));
     cudaStream_t s = (cudaStream_t)stream;
+    unsigned char* base = nullptr;
+    TRY(noalloc_scratch(s, &base));
     int64_t off = 0;
     auto carve = [&](int64_t bytes) {
         unsigned char* p = base + off;

@@ -24,7 +24,7 @@ EXPORTS = ["ib_opts_default", "ib_build_stencils", "ib_table_free", "ib_table_st
            "ib_forward_noalloc", "ib_mlp_create", "ib_mlp_free", "ib_mlp_info", "ib_mlp_buffers",
            "ib_mlp_sync_weights", "ib_mlp_features", "ib_mlp_forward", "ib_mlp_train_step",
            "ib_mlp_targets", "ib_build_stencils_learned", "ib_table_learned", "ib_forward_batch_ckpt",
-           "ib_adjoint_batch", "ib_selftest_bounded_wait"]
+           "ib_adjoint_batch", "ib_selftest_bounded_wait", "ib_stability"]
 
 
 class IbError(RuntimeError):
@@ -146,6 +146,8 @@ def load(path=LIB_PATH):
     L.ib_build_stencils_learned.restype = i32
     L.ib_table_learned.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), vp]
     L.ib_table_learned.restype = i32
+    L.ib_stability.argtypes = [vp, vp, vp, i32, dbl, i32, ctypes.c_uint64, dbl, ctypes.POINTER(dbl), vp]
+    L.ib_stability.restype = i32
     _LIB = L
     return L
 
@@ -270,7 +272,8 @@ class Mlp:
         cfg.n_hidden = int(n_hidden)
         cfg.n_layers = int(n_layers)
         cfg.in_radius = float(in_radius)
-        cfg.out_radius = float(out_radius if out_radius is not None else (min(space_order, 4) + 1) / 2.0)
+        basis = space_order if ndim == 2 else min(space_order, 4)
+        cfg.out_radius = float(out_radius if out_radius is not None else (basis + 1) / 2.0)
         self.cfg = cfg
         h = ctypes.c_void_p()
         _check(L.ib_mlp_create(ctypes.byref(cfg), ctypes.byref(h)))
@@ -482,6 +485,16 @@ def ib_adjoint_batch(tables, shots, dt, nt, ckpts, n_ckpt, residuals, stream=Non
 def ib_selftest_bounded_wait(stream=None):
     """Status of the bounded-wait self-test (IB_ERR_TIMEOUT when the bound works)."""
     return load().ib_selftest_bounded_wait(_stream(stream))
+
+
+def ib_stability(table, vel, dt, n_steps, rho=None, seed=1, max_gain=100.0, stream=None):
+    """(per-step growth estimate, status): power iteration of the time stepping
+    with the table's operators; status IB_ERR_UNSTABLE when growth^n_steps > max_gain."""
+    g = ctypes.c_double(0.0)
+    st = load().ib_stability(table.handle, _ptr(vel), _ptr(rho), _prec(vel.dtype), float(dt), int(n_steps),
+                             int(seed), float(max_gain), ctypes.byref(g), _stream(stream))
+    _check(st, allow=(IB_ERR_UNSTABLE,))
+    return g.value, st
 
 
 def ib_sync_status(stream=None):

@@ -192,37 +192,40 @@ def _odd_poly_value(x, z, z0, coeffs):
 @pytest.mark.parametrize("bc", ["free", "rigid"])
 @pytest.mark.parametrize("M", [4, 8])
 def test_flat_polynomial_exactness(bc, M):
-    """A polynomial of degree <= the basis order that satisfies every imposed
-    condition on the plane (odd in z - z0 for the free surface, even for the
-    rigid one) is differentiated exactly by the modified operator: L_mod q at
-    every IB row equals lap q."""
+    """A polynomial of degree <= a row's basis order that satisfies every
+    imposed condition on the plane (odd in z - z0 for the free surface, even
+    for the rigid one) is differentiated exactly by the modified operator:
+    L_mod q at that IB row equals lap q.  Checked for every basis order the
+    rows were fitted at (the full order, or a reduced one)."""
     nx, nz, z0 = 40, 30, 9.37
     sdf = inputs.flat_surface_sdf((nx, nz), 1.0, z0)
     geom = stencils.Geometry(sdf, 1.0, M)
     opts = stencils.Opts(M)
     L, rows = operators.laplacian_matrix(geom, bc, opts)
-    P = opts.ib_order
-    rng = np.random.default_rng(11)
-    par = 1 if bc == "free" else 0
-    coeffs = {(i, j): rng.normal() for i in range(P + 1) for j in range(P + 1 - i) if j % 2 == par}
     X, Z = np.meshgrid(np.arange(nx, dtype=float), np.arange(nz, dtype=float))
     xs, zs = (X - 20.0) / 10.0, Z / 10.0
-    q = _odd_poly_value(xs, zs, z0 / 10.0, coeffs) * geom.mask
-    # exact Laplacian of q in grid units (x, z scaled by 1/10)
-    lap = np.zeros_like(q)
-    for (i, j), c in coeffs.items():
-        if i >= 2:
-            lap += c * i * (i - 1) * xs ** (i - 2) * (zs - z0 / 10.0) ** j / 100.0
-        if j >= 2:
-            lap += c * j * (j - 1) * xs ** i * (zs - z0 / 10.0) ** (j - 2) / 100.0
-    Lq = (L @ q.ravel()).reshape(q.shape)
     ib = np.array([[z, x] for (x, z) in rows])
-    got = Lq[ib[:, 0], ib[:, 1]]
-    want = lap[ib[:, 0], ib[:, 1]]
-    # ignore the two columns nearest each side wall (truncated by the array edge)
-    keep = (ib[:, 1] >= M) & (ib[:, 1] < nx - M)
-    scale = np.abs(q).max()
-    np.testing.assert_allclose(got[keep], want[keep], atol=1e-9 * scale)
+    order = np.array([info["order"] for (_, info) in rows.values()])
+    assert (order == opts.basis(2)).any()
+    par = 1 if bc == "free" else 0
+    for P in sorted(set(order.tolist())):
+        rng = np.random.default_rng(11 + P)
+        coeffs = {(i, j): rng.normal() for i in range(P + 1) for j in range(P + 1 - i) if j % 2 == par}
+        q = _odd_poly_value(xs, zs, z0 / 10.0, coeffs) * geom.mask
+        # exact Laplacian of q in grid units (x, z scaled by 1/10)
+        lap = np.zeros_like(q)
+        for (i, j), c in coeffs.items():
+            if i >= 2:
+                lap += c * i * (i - 1) * xs ** (i - 2) * (zs - z0 / 10.0) ** j / 100.0
+            if j >= 2:
+                lap += c * j * (j - 1) * xs ** i * (zs - z0 / 10.0) ** (j - 2) / 100.0
+        Lq = (L @ q.ravel()).reshape(q.shape)
+        got = Lq[ib[:, 0], ib[:, 1]]
+        want = lap[ib[:, 0], ib[:, 1]]
+        # ignore the columns nearest each side wall (truncated by the array edge)
+        keep = (ib[:, 1] >= M) & (ib[:, 1] < nx - M) & (order == P)
+        scale = np.abs(q).max()
+        np.testing.assert_allclose(got[keep], want[keep], atol=1e-9 * scale)
 
 
 @pytest.mark.parametrize("bc", ["free", "rigid"])
