@@ -4,14 +4,20 @@
 One step = one whole shot through the C ABI: ib_build_stencils (boundary
 points, IB rows, constrained FP64 fits, packing) + ib_forward over all time
 steps (fused stencil + IB gather, source injection, receiver interpolation).
-The default workload is the 2D first-order staggered pressure-velocity case:
-1001 x 1001 nodes, h = 5 m, space order 8, FP32, 3000 time steps, free surface
-z_s(x) = 200 + 60 sin(2 pi x / 1500) m, four seeded layers, 12 Hz Ricker, 500
-receivers 10 m below the surface (synthetic inputs; the paper's DEM is not
-available).
+The default workload is the largest single-GPU grid of the method's
+configurations: 3D second-order acoustic, 512 x 512 x 384 nodes, h = 10 m,
+space order 8, FP32, 2000 time steps at CFL 0.45, a free surface of 12 seeded
+Gaussian hills on a 1 km datum, smooth random velocity 1500-4000 m/s, 10 Hz
+Ricker source, 256 x 256 receivers 2 h below the surface (synthetic inputs;
+the paper's DEM is not available).
 
-Prints one JSON line (see the keys below).  --impl reference times the FP64
-CPU oracle on a bounded crop of the same workload instead.
+The same JSON line carries, under "workloads", the other timed
+configurations of the method: the 1001 x 1001 staggered pressure-velocity
+shot, 48 batched 2D shots (batched vs one launch per shot), and their
+batched forward + adjoint velocity gradient.
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle on bounded
+crops of the same workload instead, on all host cores.
 """
 import argparse
 import json
@@ -38,7 +44,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="stag2d",
+    ap.add_argument("--workload", default="hills3d",
                     choices=["stag2d", "hills3d", "flat2d", "batch2d", "adjoint2d", "learned3d"])
     ap.add_argument("--train-topos", type=int, default=24, help="learned3d: training topographies")
     ap.add_argument("--epochs", type=int, default=8, help="learned3d: training epochs")
@@ -50,6 +56,8 @@ def parse():
                     help="override the grid (nx ny nz) of hills3d (profiling of smaller cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="time the chosen workload only")
+    ap.add_argument("--extra-steps", type=int, default=3, help="timed steps of each extra workload")
     return ap.parse_args()
 
 
@@ -168,29 +176,33 @@ def peaks():
     return 6800.0, "fallback"
 
 
+ENTRY_BYTES = {4: 4 + 2, 8: 8 + 2}   # one weight + one 16-bit footprint code per correction entry
+
+
 def kernel_bytes(w, stats, precision_bytes=4):
-    """Algorithmic DRAM bytes of one launch of each time-step kernel: every
-    array the kernel must touch read or written once, plus its correction
-    tables (weight + column offset per entry, row index/pointer/tile-order per
-    row) and one field value per correction entry."""
+    """Algorithmic DRAM bytes of one launch of each time-step kernel, counted
+    as the method's roofline counts them: every field the update must read or
+    write once per grid point, plus the correction tables at one weight and
+    one 16-bit footprint code per entry.  Second order: read p, p_prev, K and
+    write p_next (16 B per point in FP32).  Staggered, per step (v and p
+    kernels fused): read p, v_x, v_z, rho c^2, write p, v_x, v_z (28 B).
+    Values gathered by the corrections and re-reads of unfused kernels are
+    not counted."""
     N = grid_points(w)
     e = precision_bytes
-    rows, nnz = stats["rows"], stats["nnz"]
-
-    def ib(ops):
-        return sum(nnz[o] * (e + 8 + e) + rows[o] * (8 + 8 + 4) for o in ops)
-
+    nnz = sum(stats["nnz"])
+    tab = ENTRY_BYTES[e] * nnz
     if w["form"] == "staggered":
-        # v: read p, vx, vz, bx, bz; write vx, vz.   p: read vx, vz, p, kp; write p.
-        v, p = 7 * e * N + ib([0, 1]), 5 * e * N + ib([2, 3])
+        step = 7 * e * N + tab
         # the time loop runs as replays of a captured graph of 50 steps (v + p each)
-        return {"stag_v2d_f32": v, "stag_p2d_f32": p, "stag_graph50_f32": 50 * (v + p)}
+        return {"stag_graph50_" + ("f64" if e == 8 else "f32"): 50 * step}
     name = "leap%dd_%s" % (len(w["shape"]), "f64" if e == 8 else "f32")
-    # read p, p_prev, K; write p_next
-    b = 4 * e * N + ib([0])
+    b = 4 * e * N + tab
     out = {name: b}
     if len(w["shape"]) == 3 and e == 4:
-        out["leap3d_tma_f32"] = b     # same work, planes staged by TMA
+        out["leap3d_tma_f32"] = b     # the TMA-staged kernel does the same work
+    if len(w["shape"]) == 2 and e == 4:
+        out["leap2d_strip_f32"] = b
     return out
 
 
@@ -218,111 +230,179 @@ def dram_traffic(kernel):
 # ---------------------------------------------------------------------------
 # oracle (CPU) sample
 # ---------------------------------------------------------------------------
-def oracle_sample(workload, bc, full=None):
-    """Time the FP64 oracle on a bounded crop of the workload and scale it to
-    the full workload: per-IB-row build cost x the full workload's IB rows +
-    per-point-step propagation cost x its points x steps.
+def oracle_full_sizes(workload, w):
+    """(grid points, time steps, IB rows) of the full workload, the rows found by
+    the oracle's own node detection on the full mask."""
+    from oracle import stencils
+    M = w["M"]
+    if workload == "stag2d":
+        g = stencils.Geometry(w["sdf"], w["h"], M)
+        rows = (len(stencils.gradient_ib_nodes(g, 0, M)) + len(stencils.gradient_ib_nodes(g, 1, M))
+                + len(stencils.divergence_ib_nodes(g, M)))
+    else:
+        rows = len(stencils.laplacian_ib_nodes(w["sdf"] > 0, M))
+    return grid_points(w), w["nt"], rows
+
+
+def oracle_sample(workload, bc, Nf, ntf, rows_full, seed=0, build_rows=160):
+    """Time the FP64 oracle on a bounded sample of the workload and scale it to
+    the full workload: the fit of `build_rows` seeded random IB rows of a crop
+    (per-row cost x the full workload's IB rows) + time steps on the crop
+    (per point-step cost x points x steps).  Touches no GPU.
     Returns (updates/s for the full workload, description)."""
     import numpy as np
     from paper_2309_03600_gb300 import inputs
-    from oracle import sim, stencils
-    if full is None:
-        full = make_workload(workload, bc)
+    from oracle import operators, propagate, stencils
+    rng = np.random.default_rng(1000 + seed)
     if workload == "stag2d":
-        nx = nz = 161
-        nts = 300
-        w = inputs.workload_sinusoid_staggered(nx=nx, nz=nz, h=5.0, M=8, nt=nts, bc=bc)
-        w["src"] = np.array([[400.0, 500.0]])
+        M, h, nts = 8, 5.0, 200
+        w = inputs.workload_sinusoid_staggered(nx=161, nz=161, h=h, M=M, nt=nts, bc=bc)
+        geom = stencils.Geometry(w["sdf"], h, M)
+        opts = stencils.Opts(M)
+        nodes = stencils.divergence_ib_nodes(geom, M)
+        pick = [nodes[i] for i in rng.choice(len(nodes), size=min(build_rows, len(nodes)), replace=False)]
         t0 = time.perf_counter()
-        s = sim.Staggered(w["sdf"], w["vel"], w["rho"], 5.0, 8, bc, w["dt"], w["src"], w["rec"][:80])
+        div = stencils.divergence_rows(geom, bc, opts, pick)
         t1 = time.perf_counter()
-        s.forward(w["wavelet"], nts)
+        G, D, _, _ = operators.staggered_matrices(geom, bc, opts, grad_rows=[{}, {}], div_rows=div)
+        bv, kp = propagate.staggered_coefficients(geom, w["vel"], w["rho"], w["dt"])
+        S = np.zeros(kp.shape[0])
+        R = propagate.multilinear_matrix(w["rec"][:50], h, geom.sdf.shape, geom.mask)
         t2 = time.perf_counter()
-        rows = sum(len(r) for r in s.grad_rows) + len(s.div_rows)
-        g = stencils.Geometry(full["sdf"], full["h"], 8)
-        rows_full = (len(stencils.gradient_ib_nodes(g, 0, 8)) + len(stencils.gradient_ib_nodes(g, 1, 8))
-                     + len(stencils.divergence_ib_nodes(g, 8)))
-    elif workload == "hills3d":
-        nx = ny = 48
-        nz = 40
-        nts = 40
-        prm = inputs.hills_params(3, 3, (nx - 1) * 10.0, (ny - 1) * 10.0, hmin=20, hmax=80, smin=80, smax=200)
-        sdf, zs = inputs.heightfield_sdf_3d(nx, ny, nz, 10.0, inputs.hills_surface(prm, datum=150.0, zmin=40.0))
-        vel = np.full(sdf.shape, 2000.0)
-        dt = 0.45 * 10.0 / 2000.0
-        t0 = time.perf_counter()
-        s = sim.Leapfrog(sdf, vel, 10.0, 8, bc, dt, np.array([[240.0, 240.0, 300.0]]),
-                         np.array([[100.0, 100.0, zs[10, 10] + 20.0]]))
-        t1 = time.perf_counter()
-        s.forward(inputs.ricker(10.0, dt, nts), nts)
-        t2 = time.perf_counter()
-        rows = len(s.rows)
-        rows_full = len(stencils.laplacian_ib_nodes(full["sdf"] > 0, 8))
-        nz = nz
+        propagate.forward_staggered(G, D, bv, kp, S, w["wavelet"], R, nts)
+        t3 = time.perf_counter()
+        nrow = len(pick)
     else:
-        w = inputs.workload_flat2d(bc=bc)
-        nx, nz = 201, 201
-        nts = 500
+        if workload == "hills3d":
+            M, h, nts = 8, 10.0, 200
+            nx = ny = 48
+            nz = 40
+            prm = inputs.hills_params(3, 3 + seed, (nx - 1) * h, (ny - 1) * h, hmin=20, hmax=80, smin=80, smax=200)
+            sdf, _ = inputs.heightfield_sdf_3d(nx, ny, nz, h, inputs.hills_surface(prm, datum=150.0, zmin=40.0))
+            vel = np.full(sdf.shape, 2000.0)
+            dt = 0.45 * h / 2000.0
+        else:
+            w = inputs.workload_flat2d(bc=bc)
+            M, h, nts, sdf, vel, dt = w["M"], w["h"], 500, w["sdf"], w["vel"], w["dt"]
+        geom = stencils.Geometry(sdf, h, M)
+        opts = stencils.Opts(M)
+        nodes = stencils.laplacian_ib_nodes(geom.mask, M)
+        pick = [nodes[i] for i in rng.choice(len(nodes), size=min(build_rows, len(nodes)), replace=False)]
         t0 = time.perf_counter()
-        s = sim.Leapfrog(w["sdf"], w["vel"], w["h"], w["M"], bc, w["dt"], w["src"], w["rec"])
+        rows = stencils.laplacian_rows(geom, bc, opts, pick)
         t1 = time.perf_counter()
-        s.forward(w["wavelet"], nts)
+        L, _ = operators.laplacian_matrix(geom, bc, opts, ib_rows=rows)
+        K = propagate.leapfrog_coefficient(vel, dt, geom.mask)
+        S = np.zeros(K.shape[0])
+        S[K.shape[0] // 2] = 1.0
+        R = propagate.multilinear_matrix(np.array([[h * 10.0] * sdf.ndim]), h, sdf.shape, geom.mask)
         t2 = time.perf_counter()
-        rows = rows_full = len(s.rows)
-    npts = int(np.prod(s.geom.sdf.shape))
-    t_row = (t1 - t0) / max(rows, 1)
-    t_pt = (t2 - t1) / (npts * nts)
-    Nf = grid_points(full)
-    total = t_row * rows_full + t_pt * Nf * full["nt"]
-    desc = ("oracle build (%d IB rows, %.2f s) + %d steps (%.2f s) on a %s crop, scaled to %d IB rows and "
-            "%d points x %d steps" % (rows, t1 - t0, nts, t2 - t1, "x".join(map(str, s.geom.sdf.shape[::-1])),
-                                      rows_full, Nf, full["nt"]))
-    return Nf * full["nt"] / total, desc
+        propagate.forward_leapfrog(L, K, S, inputs.ricker(10.0, dt, nts), R, nts)
+        t3 = time.perf_counter()
+        nrow = len(pick)
+    npts = int(np.prod(geom.sdf.shape))
+    t_row = (t1 - t0) / max(nrow, 1)
+    t_pt = (t3 - t2) / (npts * nts)
+    total = t_row * rows_full + t_pt * Nf * ntf
+    desc = ("oracle fit of %d random IB rows (%.2f s) + %d steps (%.2f s) on a %s crop, scaled to %d IB rows and "
+            "%d points x %d steps" % (nrow, t1 - t0, nts, t3 - t2, "x".join(map(str, geom.sdf.shape[::-1])),
+                                      rows_full, Nf, ntf))
+    return Nf * ntf / total, desc
+
+
+def _oracle_worker(a):
+    return oracle_sample(*a)
+
+
+def cpu_baseline(workload, bc, sizes, cores=None):
+    """The oracle as it stands on the host cores: one single-threaded process per
+    core, each timing its own seeded sample (spawned, so no GPU state is
+    inherited).  Returns the all-core throughput (sum over processes), the
+    1-core throughput (the first process alone, before the others start) and
+    the core count."""
+    import multiprocessing as mp
+    cores = cores or os.cpu_count() or 1
+    keep = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in keep:
+        os.environ[k] = "1"
+    try:
+        ctx = mp.get_context("spawn")
+        Nf, ntf, rows = sizes
+        with ctx.Pool(1) as pool:
+            v1, desc = pool.map(_oracle_worker, [(workload, bc, Nf, ntf, rows, 0)])[0]
+        with ctx.Pool(cores) as pool:
+            res = pool.map(_oracle_worker, [(workload, bc, Nf, ntf, rows, k) for k in range(cores)])
+    finally:
+        for k, v in keep.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return {"value": sum(v for v, _ in res), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "value_1core": v1, "sample": "per process: " + desc}
 
 
 # ---------------------------------------------------------------------------
-def main():
-    args = parse()
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+def roofline_of(prof, kb, peak, peak_kind, prefer=None):
+    """Roofline of the dominant sampled kernel (most total time) among those
+    whose algorithmic bytes are known."""
+    dom, dom_t = None, -1.0
+    for name, d in prof.items():
+        if d["sampled"] and name in kb and (prefer is None or name in prefer):
+            tot = d["sampled_ms"] / d["sampled"] * d["launches"]
+            if tot > dom_t:
+                dom, dom_t = name, tot
+    if dom is None:
+        return None
+    avg_s = prof[dom]["sampled_ms"] / prof[dom]["sampled"] * 1e-3
+    ach = kb[dom] / avg_s / 1e9
+    return {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "peak_kind": peak_kind, "unit": "GB/s",
+            "frac": ach / peak, "traffic": dram_traffic(dom), "algorithmic_bytes_per_launch": kb[dom],
+            "avg_launch_us": avg_s * 1e6, "frac_of_nominal_8TBs": ach / 8000.0}
 
-    if args.impl == "reference":
-        if rank != 0:
-            return 0
-        full = make_workload(args.workload, args.bc)
-        vals, desc = [], ""
-        for i in range(args.warmup + args.steps):
-            v, desc = oracle_sample(args.workload, args.bc, full)
-            if i >= args.warmup:
-                vals.append(v)
-        val = sum(vals) / len(vals)
-        ms = 1e3 * grid_points(full) * full["nt"] / val
-        print(json.dumps({
-            "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": args.workload, "sample": desc},
-            "cpu_baseline": {"kind": "oracle", "value": val, "unit": UNIT, "cores": 1, "sample": desc},
-            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
-        return 0
 
-    import numpy as np
+def kernel_table(prof):
+    return {k: {"launches": d["launches"], "avg_us": 1e3 * d["sampled_ms"] / d["sampled"]}
+            for k, d in prof.items() if d["sampled"]}
+
+
+def run_reference(args):
+    """The oracle on the host cores: each step is one all-core sample of the
+    workload (see cpu_baseline); rank 0 alone runs."""
+    wl = args.workload if args.workload in ("hills3d", "stag2d", "flat2d") else "hills3d"
+    if wl == "hills3d":
+        from paper_2309_03600_gb300 import inputs
+        full = inputs.workload_hills3d(bc=args.bc, device="cpu")
+        full["form"] = "second"
+    else:
+        full = make_workload(wl, args.bc)
+    sizes = oracle_full_sizes(wl, full)
+    vals, base = [], None
+    for i in range(args.warmup + args.steps):
+        base = cpu_baseline(wl, args.bc, sizes)
+        if i >= args.warmup:
+            vals.append(base["value"])
+    val = sum(vals) / len(vals)
+    ms = 1e3 * sizes[0] * sizes[1] / val
+    base["value"] = val
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": wl, "sample": base["sample"]},
+        "cpu_baseline": base,
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+    return 0
+
+
+def run_single(args, workload, steps, warmup, world, rank, local, dev, dist, with_e2e, with_cpu):
+    """One workload of a single shot per rank: timed build + forward, roofline
+    of its dominant step kernel, optionally e2e through host buffers and the
+    oracle's CPU baseline.  Returns the result dict (rank 0) or None."""
     import torch
     from paper_2309_03600_gb300 import ib
 
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=dev)
-    if args.workload in ("batch2d", "adjoint2d"):
-        return run_shots(args, world, rank, local, dev, dist)
-    if args.workload == "learned3d":
-        return run_learned(args, world, rank, local, dev, dist)
-
-    w = make_workload(args.workload, args.bc, rank, args.nt, args.grid)
+    w = make_workload(workload, args.bc, rank, args.nt, args.grid if workload == "hills3d" else None)
     dtype = torch.float64 if w["dtype"] == "f64" else torch.float32
     eb = 8 if dtype == torch.float64 else 4
     nt = w["nt"]
@@ -346,7 +426,7 @@ def main():
         return t
 
     tab = None
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         flush.zero_()
         tab = step()
     torch.cuda.synchronize()
@@ -360,7 +440,7 @@ def main():
     clocks.start()
     ev = []
     wall0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -374,6 +454,12 @@ def main():
         dist.barrier()
     clk = clocks.stop()
     prof = ib.ib_profile()
+    ib.ib_profile_enable(0)
+    # the run must have stayed finite (end-of-run NaN/Inf check and the traces)
+    ib.ib_sync_status()
+    finite = bool(torch.isfinite(traces).all())
+    if not finite:
+        raise RuntimeError("non-finite traces in the timed run of " + workload)
     stats = tab.stats()
     ms_steps = [a.elapsed_time(b) for a, b in ev]
     ms = max_over_ranks(sum(ms_steps) / len(ms_steps), dist, dev)
@@ -381,37 +467,17 @@ def main():
     upd_per_step = N * nt
     value = job_value(world, upd_per_step, ms)
     launches = sum(d["launches"] for d in prof.values())
-    # ---- roofline of the dominant kernel
-    kb = kernel_bytes(w, stats, eb)
-    dom, dom_t = None, -1.0
-    for name, d in prof.items():
-        if d["sampled"] and name in kb:
-            avg = d["sampled_ms"] / d["sampled"]
-            tot = avg * d["launches"]
-            if tot > dom_t:
-                dom, dom_t = name, tot
     peak, peak_kind = peaks()
-    roof = None
-    kernels = {}
-    for name, d in prof.items():
-        if d["sampled"]:
-            kernels[name] = {"launches": d["launches"], "avg_us": 1e3 * d["sampled_ms"] / d["sampled"]}
-    if dom:
-        avg_s = prof[dom]["sampled_ms"] / prof[dom]["sampled"] * 1e-3
-        ach = kb[dom] / avg_s / 1e9
-        roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "peak_kind": peak_kind,
-                "unit": "GB/s", "frac": ach / peak, "traffic": dram_traffic(dom),
-                "algorithmic_bytes_per_launch": kb[dom], "avg_launch_us": avg_s * 1e6,
-                "frac_of_nominal_8TBs": ach / 8000.0}
+    roof = roofline_of(prof, kernel_bytes(w, stats, eb), peak, peak_kind)
     # ---- end to end through the C ABI with host buffers
     e2e = None
-    if not args.no_e2e:
+    if with_e2e:
         traces_h = torch.empty((rec.shape[0], nt), dtype=dtype).pin_memory()
         e2e_ms = []
         h2d = sum(t.numel() * t.element_size() for t in (sdf_h, vel_h, wav_h, src_h, rec_h) if t is not None)
         if rho_h is not None:
             h2d += rho_h.numel() * rho_h.element_size()
-        for _ in range(max(2, min(args.steps, 3))):
+        for _ in range(max(2, min(steps, 3))):
             flush.zero_()
             torch.cuda.synchronize()
             t0 = time.perf_counter()
@@ -427,26 +493,81 @@ def main():
                "d2h_bytes_per_step": int(traces_h.numel() * traces_h.element_size()), "ms_per_step": em}
     # ---- CPU oracle baseline (rank 0, one GPU)
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        v, desc = oracle_sample(args.workload, args.bc, w)
-        cpu = {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": desc}
+    if with_cpu and rank == 0 and world == 1:
+        cpu = cpu_baseline(workload, args.bc, oracle_full_sizes(workload, w))
     if rank != 0:
-        return 0
+        return None
     setup_rows = sum(stats["rows"])
-    out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": w["dtype"], "data": "synthetic",
-        "config": {"workload": args.workload, "desc": w["desc"], "grid": list(w["shape"]), "nt": nt,
+    return {
+        "value": value, "ms_per_step": ms, "dtype": w["dtype"],
+        "config": {"workload": workload, "desc": w["desc"], "grid": list(w["shape"]), "nt": nt,
                    "space_order": M, "bc": args.bc, "ib_rows": stats["rows"], "ib_nnz": stats["nnz"],
-                   "l2": "flushed between steps (256 MB write)", "parallelism": "replicas" if world > 1 else "single"},
+                   "l2": "flushed between steps (256 MB write)",
+                   "parallelism": "replicas" if world > 1 else "single"},
         "setup": {"ib_rows": setup_rows, "seconds": stats["setup_seconds"],
                   "ib_rows_per_s": setup_rows / max(stats["setup_seconds"], 1e-9),
                   "rows_grown": stats["n_grown"], "rows_order_reduced": stats["n_reduced"],
                   "rank_failures": stats["n_rank_failures"], "boundary_points": stats["n_boundary_points"]},
-        "roofline": roof, "kernels": kernels, "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
-        "gpu_launches": int(launches), "wall_s": wall,
+        "roofline": roof, "kernels": kernel_table(prof), "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
+        "gpu_launches": int(launches), "wall_s": wall, "finite": finite,
     }
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        return run_reference(args)
+
+    import torch
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    if args.workload == "learned3d":
+        return run_learned(args, world, rank, local, dev, dist)
+    if args.workload in ("batch2d", "adjoint2d"):
+        res = run_shots(args, args.workload, args.steps, args.warmup, world, rank, local, dev, dist)
+    else:
+        res = run_single(args, args.workload, args.steps, args.warmup, world, rank, local, dev, dist,
+                         not args.no_e2e, not args.no_cpu_baseline)
+    extras = {}
+    if not args.no_extras and args.workload == "hills3d" and not args.nt and not args.grid:
+        ex_steps = max(1, args.extra_steps)
+        for name in ("stag2d", "batch2d", "adjoint2d"):
+            if name == "stag2d":
+                r = run_single(args, name, ex_steps, max(3, args.warmup), world, rank, local, dev, dist, False,
+                               False)
+            else:
+                r = run_shots(args, name, ex_steps, max(3, args.warmup), world, rank, local, dev, dist)
+            if r is not None:
+                extras[name] = {k: r[k] for k in ("value", "ms_per_step", "config", "setup", "roofline", "kernels",
+                                                  "compare", "clocks", "gpu_launches") if k in r}
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    out = {
+        "metric": METRIC, "value": res["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": res["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": res["dtype"], "data": "synthetic",
+    }
+    for k in ("config", "setup", "roofline", "kernels", "compare", "e2e", "cpu_baseline", "clocks", "finite"):
+        if k in res:
+            out[k] = res[k]
+    launches = res["gpu_launches"] + sum(e.get("gpu_launches", 0) for e in extras.values())
+    out["gpu_launches"] = int(res["gpu_launches"])
+    if extras:
+        out["workloads"] = extras
+        out["gpu_launches_all_workloads"] = int(launches)
     print(json.dumps(out))
     if dist:
         dist.destroy_process_group()
@@ -604,7 +725,7 @@ def run_learned(args, world, rank, local, dev, dist):
     return 0
 
 
-def run_shots(args, world, rank, local, dev, dist):
+def run_shots(args, workload, steps, warmup, world, rank, local, dev, dist):
     """batch2d: many 2D second-order shots (sides in [400, 1200], order 8, FP32,
     2000 steps) in one batched, graph-captured launch per step; one step = the
     forward of all shots (tables built once, reported as setup).  The same shots
@@ -612,7 +733,8 @@ def run_shots(args, world, rank, local, dev, dist):
     adjoint2d: the same shots, batched forward with 40 checkpoints + batched
     adjoint (velocity gradient of the L2 misfit, the whole backward pass one
     captured graph); one step = all shots.  The same shots one ib_forward +
-    ib_adjoint call per shot are timed once for comparison."""
+    ib_adjoint call per shot are timed once for comparison.
+    Returns the result dict (rank 0) or None."""
     import torch
     from paper_2309_03600_gb300 import ib, inputs
     nt = args.nt or 2000
@@ -633,13 +755,15 @@ def run_shots(args, world, rank, local, dev, dist):
                           N=w["shape"][0] * w["shape"][1], dt=w["dt"]))
     dt = shots[0]["dt"]
     N = sum(sh["N"] for sh in shots)
+    nnz = sum(sum(t.stats()["nnz"]) for t in tables)
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
     n_ckpt = 40
     ckpts = []
-    if args.workload == "adjoint2d":
+    if workload == "adjoint2d":
         for t in tables:
             ckpts.append(torch.empty(ib.ib_checkpoint_bytes(t, 32, nt, n_ckpt), dtype=torch.uint8, device=dev))
+    last = {}
 
     def per_shot_adjoint():
         for t, sh, ck in zip(tables, shots, ckpts):
@@ -648,14 +772,14 @@ def run_shots(args, world, rank, local, dev, dist):
             ib.ib_adjoint(t, sh["vel"], sh["wavelet"], sh["src"], sh["rec"], dt, nt, ck, n_ckpt, tr)
 
     def step():
-        if args.workload == "batch2d":
-            ib.ib_forward_batch(tables, shots, dt, nt)
+        if workload == "batch2d":
+            last["out"] = ib.ib_forward_batch(tables, shots, dt, nt)
         else:
             # residual = traces (observed data zero): the misfit gradient of all shots
             outs = ib.ib_forward_batch_ckpt(tables, shots, dt, nt, ckpts, n_ckpt)
-            ib.ib_adjoint_batch(tables, shots, dt, nt, ckpts, n_ckpt, outs)
+            last["out"] = ib.ib_adjoint_batch(tables, shots, dt, nt, ckpts, n_ckpt, outs)
 
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         flush.zero_()
         step()
     torch.cuda.synchronize()
@@ -666,7 +790,7 @@ def run_shots(args, world, rank, local, dev, dist):
     torch.cuda.synchronize()
     clocks.start()
     ev = []
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush.zero_()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -679,18 +803,22 @@ def run_shots(args, world, rank, local, dev, dist):
         dist.barrier()
     clk = clocks.stop()
     prof = ib.ib_profile()
+    ib.ib_profile_enable(0)
+    ib.ib_sync_status()
+    finite = all(bool(torch.isfinite(x).all()) for x in last["out"])
+    if not finite:
+        raise RuntimeError("non-finite output in the timed run of " + workload)
     ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / len(ev), dist, dev)
     value = job_value(world, N * nt, ms)
-    kernels = {k: {"launches": d["launches"], "avg_us": 1e3 * d["sampled_ms"] / d["sampled"]}
-               for k, d in prof.items() if d["sampled"]}
     peak, peak_kind = peaks()
     roof = None
     compare = None
-    if args.workload == "batch2d":
+    eb = ENTRY_BYTES[4]
+    if workload == "batch2d":
         g = prof.get("leap2d_batch_graph_f32")
         if g and g["sampled"]:
             per_launch = g["sampled_ms"] / g["sampled"] / nt * 1e-3
-            byts = 16.0 * N + sum(t.stats()["nnz"][0] * 12 + t.stats()["rows"][0] * 20 for t in tables)
+            byts = 16.0 * N + eb * nnz
             ach = byts / per_launch / 1e9
             roof = {"bound": "hbm", "kernel": "leap2d_batch_f32", "achieved": ach, "peak": peak,
                     "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / peak, "traffic": None,
@@ -713,15 +841,17 @@ def run_shots(args, world, rank, local, dev, dist):
         a = prof.get("adj2d_batch_graph_f32")
         if a and a["sampled"]:
             avg = a["sampled_ms"] / a["sampled"] * 1e-3
-            # one replay = the backward pass of all shots: per step and point the adjoint
-            # kernel moves 33 B (mu, mu_prev, K, mask, three stored p, gradient
-            # read + write, mu_next) and the recompute 16 B; plus the segment restores
-            byts = nt * N * (33 + 16) + n_ckpt * 4 * N * 4
+            # one replay = the backward pass of all shots.  Per step and point: the
+            # recompute reads p, p_prev, K and stores p (16 B + the forward table);
+            # the adjoint step reads mu, mu_prev, K, the stored p^m, p^{m-1},
+            # p^{m-2}, the gradient, and writes mu_next and the gradient (36 B +
+            # the transposed table); plus the checkpoint restores (4 fields)
+            byts = nt * (N * (16 + 36) + 2 * eb * nnz) + n_ckpt * 4 * N * 4
             ach = byts / avg / 1e9
             roof = {"bound": "hbm", "kernel": "adj2d_batch_graph_f32", "achieved": ach, "peak": peak,
                     "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / peak, "traffic": None,
                     "algorithmic_bytes_per_launch": byts, "avg_launch_us": avg * 1e6,
-                    "frac_of_nominal_8TBs": ach / 8000.0, "note": "correction-table bytes not counted"}
+                    "frac_of_nominal_8TBs": ach / 8000.0}
         flush.zero_()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -734,23 +864,17 @@ def run_shots(args, world, rank, local, dev, dist):
         compare = {"per_shot_calls_value": N * nt / (ms1 * 1e-3), "per_shot_calls_ms": ms1,
                    "batched_speedup": ms1 / ms}
     if rank != 0:
-        return 0
-    out = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": args.workload, "shots": len(shots), "points": N, "nt": nt, "space_order": 8,
-                   "step": ("batched forward of all shots (tables prebuilt)" if args.workload == "batch2d"
+        return None
+    return {
+        "value": value, "ms_per_step": ms, "dtype": "f32",
+        "config": {"workload": workload, "shots": len(shots), "points": N, "nt": nt, "space_order": 8,
+                   "step": ("batched forward of all shots (tables prebuilt)" if workload == "batch2d"
                             else "batched forward with 40 checkpoints + batched adjoint gradient, all shots"),
                    "l2": "flushed between steps (256 MB write)"},
-        "setup": {"seconds": t_setup, "ib_rows": sum(t.stats()["rows"][0] for t in tables)},
-        "roofline": roof, "kernels": kernels, "compare": compare, "e2e": None, "cpu_baseline": None,
-        "clocks": clk, "gpu_launches": int(sum(d["launches"] for d in prof.values())),
+        "setup": {"seconds": t_setup, "ib_rows": sum(t.stats()["rows"][0] for t in tables), "ib_nnz": nnz},
+        "roofline": roof, "kernels": kernel_table(prof), "compare": compare, "e2e": None, "cpu_baseline": None,
+        "clocks": clk, "gpu_launches": int(sum(d["launches"] for d in prof.values())), "finite": finite,
     }
-    print(json.dumps(out))
-    if dist:
-        dist.destroy_process_group()
-    return 0
 
 
 if __name__ == "__main__":

@@ -67,3 +67,8 @@ def cuda(a, dtype=torch.float64):
 
 def rel_l2(a, b):
     return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+def record(name, **vals):
+    """Print a measured parity figure (collected from the test log to set tolerances)."""
+    print("PARITY %s %s" % (name, " ".join("%s=%.3e" % (k, v) for k, v in vals.items())), flush=True)

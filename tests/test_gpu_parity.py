@@ -7,7 +7,7 @@ import torch
 
 from oracle import sim, stencils
 from paper_2309_03600_gb300 import inputs
-from gpu_util import compare_tables, cuda, gpu_rows, rel_l2
+from gpu_util import compare_tables, cuda, gpu_rows, record, rel_l2
 
 # FP64 traces: the library's weights come from its own FP64 factorisation
 # (Cholesky factor of the streamed Gram matrix, seminormal equations + one
@@ -84,10 +84,11 @@ def test_table_sinusoid2d_basis8():
     compare_tables(orc, gpu, rtol=1e-7)
 
 
+@pytest.mark.parametrize("bc", ["free", "rigid"])
 @pytest.mark.parametrize("M", [4, 8])
-def test_table_hills3d(M):
+def test_table_hills3d(M, bc):
     sdf, _ = small_hills()
-    orc, gpu, _ = _lap_case(sdf, 10.0, M, "free")
+    orc, gpu, _ = _lap_case(sdf, 10.0, M, bc)
     assert len(orc) > 300
     compare_tables(orc, gpu, rtol=1e-8)
 
@@ -138,6 +139,7 @@ def test_forward_flat2d_201(bc):
     ref = _oracle_leap(w, bc)
     e64 = rel_l2(_run_leap(w, bc, torch.float64), ref)
     e32 = rel_l2(_run_leap(w, bc, torch.float32), ref)
+    record("flat2d_201_" + bc, e64=e64, e32=e32)
     assert e64 < TOL64, e64
     assert e32 < TOL32, e32
 
@@ -151,12 +153,14 @@ def test_forward_sinusoid2d_order8(bc):
     ref = _oracle_leap(w, bc)
     e64 = rel_l2(_run_leap(w, bc, torch.float64), ref)
     e32 = rel_l2(_run_leap(w, bc, torch.float32), ref)
+    record("sinusoid2d_order8_" + bc, e64=e64, e32=e32)
     assert e64 < TOL64, e64
     assert e32 < TOL32, e32
 
 
+@pytest.mark.parametrize("bc", ["free", "rigid"])
 @pytest.mark.parametrize("M", [4, 8])
-def test_forward_hills3d(M):
+def test_forward_hills3d(M, bc):
     sdf, zs = small_hills()
     h = 10.0
     nx, ny, nz = 40, 36, 34
@@ -166,9 +170,10 @@ def test_forward_hills3d(M):
     src = np.array([[20 * h, 17 * h, 26 * h]])
     rec = np.array([[x * h, y * h, zs[y, x] + 2 * h] for x in range(4, 36, 5) for y in range(4, 32, 5)])
     w = dict(sdf=sdf, vel=vel, h=h, M=M, dt=dt, nt=nt, src=src, rec=rec, wavelet=inputs.ricker(25.0, dt, nt))
-    ref = _oracle_leap(w, "free")
-    e32 = rel_l2(_run_leap(w, "free", torch.float32), ref)
-    e64 = rel_l2(_run_leap(w, "free", torch.float64), ref)
+    ref = _oracle_leap(w, bc)
+    e32 = rel_l2(_run_leap(w, bc, torch.float32), ref)
+    e64 = rel_l2(_run_leap(w, bc, torch.float64), ref)
+    record("hills3d_M%d_%s" % (M, bc), e64=e64, e32=e32)
     assert e64 < TOL64, e64
     assert e32 < TOL32, e32
 
@@ -189,6 +194,7 @@ def test_forward_staggered2d(bc, M):
         out[dt_] = tr.double().cpu().numpy()
     e64 = rel_l2(out[torch.float64], ref)
     e32 = rel_l2(out[torch.float32], ref)
+    record("staggered2d_M%d_%s" % (M, bc), e64=e64, e32=e32)
     assert e64 < TOL64, e64
     assert e32 < TOL32, e32
 
@@ -227,8 +233,10 @@ def test_adjoint_vs_oracle(bc, n_ckpt):
     g, gw = ib.ib_adjoint(t, v, cuda(wv), cuda(src), cuda(rec), dt, nt, ck, n_ckpt, cuda(res),
                           want_wavelet_grad=True)
     ib.ib_sync_status()
-    assert rel_l2(g.cpu().numpy().ravel(), g_ref) < TOL64
-    assert rel_l2(gw.cpu().numpy(), gw_ref) < TOL64
+    eg, ew = rel_l2(g.cpu().numpy().ravel(), g_ref), rel_l2(gw.cpu().numpy(), gw_ref)
+    record("adjoint64_%s_ck%d" % (bc, n_ckpt), grad=eg, wavelet=ew)
+    assert eg < TOL64
+    assert ew < TOL64
 
 
 def test_adjoint_dot_product_fp32():
@@ -263,7 +271,9 @@ def test_autograd_function():
     s = sim.Leapfrog(sdf, vel, h, M, "free", dt, src, rec)
     ref_tr, hist = s.forward(wv, nt, keep_history=True)
     g_ref, _ = s.adjoint(ref_tr, hist)
-    assert rel_l2(v.grad.detach().cpu().numpy().ravel(), g_ref) < TOL64
+    e = rel_l2(v.grad.detach().cpu().numpy().ravel(), g_ref)
+    record("autograd64", grad=e)
+    assert e < TOL64
 
 
 # ---------------------------------------------------------------------------
@@ -294,7 +304,9 @@ def test_forward_many_sources():
     tr = ib.ib_forward(t, cuda(w["vel"]), cuda(w["wavelet"]), cuda(src), cuda(w["rec"]), w["dt"], 150)
     ref = sim.Leapfrog(w["sdf"], w["vel"], w["h"], w["M"], "free", w["dt"], src, w["rec"]).forward(w["wavelet"], 150)
     assert np.abs(ref).max() > 0
-    assert rel_l2(tr.cpu().numpy(), ref) < TOL64
+    e = rel_l2(tr.cpu().numpy(), ref)
+    record("many_sources64", e64=e)
+    assert e < TOL64
     src33 = np.concatenate([src, src[:1]], axis=0)
     with pytest.raises(ib.IbError) as e:
         ib.ib_forward(t, cuda(w["vel"]), cuda(w["wavelet"]), cuda(src33), cuda(w["rec"]), w["dt"], 150)
@@ -419,3 +431,148 @@ def test_forward_3d_tma_matches_plain_loads(monkeypatch):
     assert "leap3d_f32" in ib.ib_profile()
     ib.ib_profile_enable(0)
     assert rel_l2(tma, plain) < 1e-6
+
+
+# ---------------------------------------------------------------------------
+# FP32 adjoint against the oracle, and the gradient against finite differences
+# ---------------------------------------------------------------------------
+@pytest.fixture(scope="module")
+def adjoint_case32():
+    """A shot of the batched-shot family (order 8, layered velocity, sinusoid
+    plus bump surface) at a size the oracle finishes in about a minute: the
+    oracle's FP64 traces, the residual against data from a 2 % faster model,
+    and the oracle's velocity gradient of the misfit."""
+    nt = 300
+    w = inputs.workload_shot2d(40, nt=nt, side=(140, 200))
+    vel = w["vel"].astype(np.float64)
+    s = sim.Leapfrog(w["sdf"], vel, w["h"], w["M"], "free", w["dt"], w["src"], w["rec"])
+    tr, hist = s.forward(w["wavelet"], nt, keep_history=True)
+    dobs = s.with_velocity(vel * 1.02).forward(w["wavelet"], nt)
+    res = tr - dobs
+    g_ref, _ = s.adjoint(res, hist)
+    return w, nt, res, g_ref
+
+
+def test_adjoint_fp32_vs_oracle(adjoint_case32):
+    """ib_adjoint in FP32 (the batched workload's precision): the velocity
+    gradient of the misfit against the oracle's exact discrete adjoint."""
+    w, nt, res, g_ref = adjoint_case32
+    t = ib.ib_build_stencils(cuda(w["sdf"]), w["h"], "free", "second", w["M"])
+    v = cuda(w["vel"], torch.float32)
+    wv = cuda(w["wavelet"], torch.float32)
+    n_ckpt = 10
+    ck = torch.zeros(ib.ib_checkpoint_bytes(t, 32, nt, n_ckpt), dtype=torch.uint8, device="cuda")
+    ib.ib_forward(t, v, wv, cuda(w["src"]), cuda(w["rec"]), w["dt"], nt, ckpt=ck, n_ckpt=n_ckpt)
+    g, _ = ib.ib_adjoint(t, v, wv, cuda(w["src"]), cuda(w["rec"]), w["dt"], nt, ck, n_ckpt,
+                         cuda(res, torch.float32))
+    ib.ib_sync_status()
+    e = rel_l2(g.double().cpu().numpy().ravel(), g_ref)
+    record("adjoint32_single", grad=e)
+    assert e < TOL32, e
+
+
+def test_adjoint_batch_fp32_vs_oracle(adjoint_case32):
+    """ib_forward_batch_ckpt + ib_adjoint_batch (one graph for the backward
+    pass) with a second shot beside it: shot 0's FP32 gradient against the oracle."""
+    w, nt, res, g_ref = adjoint_case32
+    w2 = inputs.workload_shot2d(41, nt=nt, side=(120, 180))
+    tables, shots = [], []
+    for ww in (w, w2):
+        tables.append(ib.ib_build_stencils(cuda(ww["sdf"]), ww["h"], "free", "second", ww["M"]))
+        shots.append(dict(vel=cuda(ww["vel"], torch.float32), wavelet=cuda(ww["wavelet"], torch.float32),
+                          src=cuda(ww["src"]), rec=cuda(ww["rec"])))
+    n_ckpt = 10
+    ckpts = [torch.empty(ib.ib_checkpoint_bytes(t, 32, nt, n_ckpt), dtype=torch.uint8, device="cuda")
+             for t in tables]
+    outs = ib.ib_forward_batch_ckpt(tables, shots, w["dt"], nt, ckpts, n_ckpt)
+    residuals = [cuda(res, torch.float32), outs[1]]
+    grads = ib.ib_adjoint_batch(tables, shots, w["dt"], nt, ckpts, n_ckpt, residuals)
+    ib.ib_sync_status()
+    e = rel_l2(grads[0].double().cpu().numpy().ravel(), g_ref)
+    record("adjoint32_batch", grad=e)
+    assert e < TOL32, e
+
+
+@pytest.mark.parametrize("bc", ["free", "rigid"])
+def test_gradient_vs_finite_difference_gpu(bc):
+    """Central finite difference of J(c) = 1/2 |F(c) - d|^2 along a random
+    direction, every J through ib_forward (FP64), against <dJ/dc, dc> from
+    ib_adjoint."""
+    sdf, vel, h, M, dt, src, rec = _tiny(bc)
+    nt = 90
+    wv = cuda(inputs.ricker(25.0, dt, nt))
+    t = ib.ib_build_stencils(cuda(sdf), h, bc, "second", M)
+    S, R = cuda(src), cuda(rec)
+    dobs = ib.ib_forward(t, cuda(vel * 1.01), wv, S, R, dt, nt)
+
+    def J(v):
+        tr = ib.ib_forward(t, cuda(v), wv, S, R, dt, nt)
+        return 0.5 * float(((tr - dobs) ** 2).sum()), tr
+
+    _, tr0 = J(vel)
+    ck = torch.zeros(ib.ib_checkpoint_bytes(t, 64, nt, 5), dtype=torch.uint8, device="cuda")
+    ib.ib_forward(t, cuda(vel), wv, S, R, dt, nt, ckpt=ck, n_ckpt=5)
+    g, _ = ib.ib_adjoint(t, cuda(vel), wv, S, R, dt, nt, ck, 5, tr0 - dobs)
+    rng = np.random.default_rng(5)
+    dv = rng.normal(size=vel.shape) * (sdf > 0)
+    eps = 1e-3
+    fd = (J(vel + eps * dv)[0] - J(vel - eps * dv)[0]) / (2 * eps)
+    an = float((g.cpu().numpy() * dv).sum())
+    ib.ib_sync_status()
+    record("gradient_fd_" + bc, rel=abs(fd - an) / abs(fd))
+    assert abs(fd - an) <= 1e-6 * abs(fd), (fd, an)
+
+
+# ---------------------------------------------------------------------------
+# more receivers than threads in a time-step launch
+# ---------------------------------------------------------------------------
+def _below_surface_points(rng, n, sdf, h, ndim):
+    """n random points (metres) inside the array whose nearest node is interior."""
+    shape = sdf.shape
+    out = []
+    while len(out) < n:
+        p = np.array([rng.uniform(0, (shape[ndim - 1 - a] - 1)) for a in range(ndim)])
+        node = tuple(int(round(x)) for x in reversed(p))
+        if sdf[node] > 0:
+            out.append(p * h)
+    return np.array(out)
+
+
+def test_forward_many_receivers_2d_and_3d():
+    """6000 (2D, 18 blocks of 256 threads) and 8000 (3D, 20 blocks) receivers:
+    every trace is recorded, as in the oracle."""
+    rng = np.random.default_rng(12)
+    w = inputs.workload_flat2d(nx=81, nz=71, nt=120, z0_cells=20.3, src_cells=(40.0, 45.0),
+                               rec_x_cells=(10, 70), rec_z_cells=30)
+    rec = _below_surface_points(rng, 6000, w["sdf"], w["h"], 2)
+    w["rec"] = rec
+    ref = _oracle_leap(w, "free")
+    e2 = rel_l2(_run_leap(w, "free", torch.float64), ref)
+    sdf, zs = small_hills()
+    h = 10.0
+    rec3 = _below_surface_points(rng, 8000, sdf, h, 3)
+    w3 = dict(sdf=sdf, vel=np.full(sdf.shape, 1800.0), h=h, M=8, dt=0.4 * h / 1800.0, nt=100,
+              src=np.array([[20 * h, 17 * h, 26 * h]]), rec=rec3)
+    w3["wavelet"] = inputs.ricker(25.0, w3["dt"], 100)
+    ref3 = _oracle_leap(w3, "free")
+    e3 = rel_l2(_run_leap(w3, "free", torch.float32), ref3)
+    record("many_receivers", e2d64=e2, e3d32=e3)
+    assert e2 < TOL64, e2
+    assert e3 < TOL32, e3
+
+
+def test_staggered_many_receivers():
+    """Staggered step with 4000 receivers on a grid of 10 step tiles."""
+    w = inputs.workload_sinusoid_staggered(nx=121, nz=81, h=5.0, M=4, nt=200)
+    rng = np.random.default_rng(13)
+    w["rec"] = _below_surface_points(rng, 4000, w["sdf"], 5.0, 2)
+    w["src"] = np.array([[300.0, 300.0]])
+    s = sim.Staggered(w["sdf"], w["vel"], w["rho"], 5.0, 4, "free", w["dt"], w["src"], w["rec"])
+    ref = s.forward(w["wavelet"], w["nt"])
+    t = ib.ib_build_stencils(cuda(w["sdf"]), 5.0, "free", "staggered", 4)
+    tr = ib.ib_forward(t, cuda(w["vel"], torch.float64), cuda(w["wavelet"]), cuda(w["src"]), cuda(w["rec"]),
+                       w["dt"], w["nt"], rho=cuda(w["rho"], torch.float64))
+    ib.ib_sync_status()
+    e = rel_l2(tr.cpu().numpy(), ref)
+    record("staggered_many_receivers", e64=e)
+    assert e < TOL64, e

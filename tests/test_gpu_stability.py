@@ -1,0 +1,117 @@
+"""GPU: stability estimates (ib_stability) against closed forms and the oracle's
+spectrum, and NaN/Inf detection at the end of a run (IB_ERR_UNSTABLE)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import operators, propagate, sim, stability, stencils
+from paper_2309_03600_gb300 import inputs
+from gpu_util import cuda
+
+pytestmark = pytest.mark.gpu
+
+ib = pytest.importorskip("paper_2309_03600_gb300.ib")
+
+
+def _closed_form_growth(nx, nz, courant):
+    """Order-2 Laplacian, zero Dirichlet edges, no boundary: the eigenvalues of
+    dt^2 c^2 L are -C^2 4 (sin^2(j pi / 2(nx+1)) + sin^2(k pi / 2(nz+1)))."""
+    sx = np.sin(np.arange(1, nx + 1) * np.pi / (2 * (nx + 1))) ** 2
+    sz = np.sin(np.arange(1, nz + 1) * np.pi / (2 * (nz + 1))) ** 2
+    mu = -courant ** 2 * 4.0 * (sx[:, None] + sz[None, :]).ravel()
+    return stability.growth_from_mu(mu)
+
+
+@pytest.mark.parametrize("courant,unstable", [(0.5, False), (0.75, True)])
+def test_stability_closed_form_order2(courant, unstable):
+    """No boundary, order 2, constant c: the estimate equals the closed-form
+    spectral radius of the leapfrog map (1 below the CFL limit 1/sqrt(2),
+    about 1.98 at C = 0.75)."""
+    nx, nz, h, c = 48, 40, 10.0, 1500.0
+    sdf = np.full((nz, nx), 1e6)
+    t = ib.ib_build_stencils(cuda(sdf), h, "free", "second", 2)
+    dt = courant * h / c
+    rho = _closed_form_growth(nx, nz, courant)
+    g, st = ib.ib_stability(t, cuda(np.full((nz, nx), c)), dt, 1000)
+    assert abs(g - rho) <= 5e-3 * rho, (g, rho)
+    assert (st == ib.IB_ERR_UNSTABLE) == unstable
+    if not unstable:
+        assert abs(rho - 1.0) < 1e-12
+
+
+def _sinusoid_leap(basis, tol):
+    ws = inputs.workload_sinusoid_staggered(nx=61, nz=75, h=5.0, M=8, nt=10)
+    geom = stencils.Geometry(ws["sdf"], 5.0, 8)
+    L, _ = operators.laplacian_matrix(geom, "free", stencils.Opts(8, ib_order=basis, rank_tol=tol))
+    vel = ws["vel"].astype(np.float64)
+    dt = 0.4 * 5.0 / vel.max()
+    K = propagate.leapfrog_coefficient(vel, dt, geom.mask)
+    return ws, vel, dt, L, K
+
+
+def test_stability_ib_matches_oracle_spectrum():
+    """Order-8 basis accepted at rank tolerance 1e-10 on the seeded sinusoid:
+    a growing mode (about 1.05 per step).  The library's power iteration
+    (FP64) finds the spectral radius the oracle's eigenvalues give."""
+    ws, vel, dt, L, K = _sinusoid_leap(8, 1e-10)
+    rho = stability.growth_from_mu(stability.leapfrog_mu(L, K))
+    assert rho > 1.01
+    o = ib.ib_opts_default(8)
+    o.basis_order = 8
+    o.rank_tol = 1e-10
+    t = ib.ib_build_stencils(cuda(ws["sdf"]), 5.0, "free", "second", 8, opts=o)
+    g, st = ib.ib_stability(t, cuda(vel), dt, 1500)
+    assert st == ib.IB_ERR_UNSTABLE
+    assert abs(g - rho) <= 2e-3, (g, rho)
+
+
+def test_stability_default_matches_oracle_power_iteration():
+    """Default options (rank tolerance 1e-3): the growth per step of the same
+    power iteration in the oracle and the library agree."""
+    ws, vel, dt, L, K = _sinusoid_leap(0, 1e-3)
+    r_orc, _ = stability.leapfrog_growth(L, K, nsteps=3000)
+    t = ib.ib_build_stencils(cuda(ws["sdf"]), 5.0, "free", "second", 8)
+    g, _ = ib.ib_stability(t, cuda(vel), dt, 3000, max_gain=1e30)
+    rho = stability.growth_from_mu(stability.leapfrog_mu(L, K))
+    # both estimates approach the spectral radius from the same side
+    assert abs(g - r_orc) <= 0.5 * (rho - 1.0) + 1e-5, (g, r_orc, rho)
+    assert g <= rho + 0.25 * (rho - 1.0), (g, rho)
+
+
+def test_stability_staggered_matches_oracle():
+    """Staggered form, order-8 basis at rank tolerance 1e-10 (a growing mode):
+    library and oracle power iterations agree."""
+    ws = inputs.workload_sinusoid_staggered(nx=61, nz=75, h=5.0, M=8, nt=10)
+    opts = stencils.Opts(8, ib_order=8, rank_tol=1e-10)
+    s = sim.Staggered(ws["sdf"], ws["vel"], ws["rho"], 5.0, 8, "free", ws["dt"], ws["src"], ws["rec"][:4],
+                      opts=opts)
+    r_orc, _ = stability.staggered_growth(s.G, s.D, s.bv, s.kp, nsteps=3000)
+    assert r_orc > 1.002
+    o = ib.ib_opts_default(8)
+    o.basis_order = 8
+    o.rank_tol = 1e-10
+    t = ib.ib_build_stencils(cuda(ws["sdf"]), 5.0, "free", "staggered", 8, opts=o)
+    g, st = ib.ib_stability(t, cuda(ws["vel"].astype(np.float64)), ws["dt"], 3000,
+                            rho=cuda(ws["rho"].astype(np.float64)))
+    assert st == ib.IB_ERR_UNSTABLE
+    assert abs(g - r_orc) <= 0.2 * (r_orc - 1.0), (g, r_orc)
+
+
+def test_nonfinite_run_reports_unstable():
+    """A time step far above the CFL limit overflows FP32 within the run: the
+    end-of-run check makes ib_sync_status return IB_ERR_UNSTABLE once, and a
+    stable run afterwards is clean."""
+    w = inputs.workload_flat2d(nx=81, nz=71, nt=300, z0_cells=20.3, src_cells=(40.0, 45.0),
+                               rec_x_cells=(10, 70), rec_z_cells=30, M=8)
+    t = ib.ib_build_stencils(cuda(w["sdf"]), w["h"], "free", "second", 8)
+    args = (cuda(w["vel"], torch.float32), cuda(w["wavelet"], torch.float32), cuda(w["src"]), cuda(w["rec"]))
+    ib.ib_forward(t, *args, 1.5 * w["h"] / w["c"], 300)
+    with pytest.raises(ib.IbError) as e:
+        ib.ib_sync_status()
+    assert e.value.status == ib.IB_ERR_UNSTABLE
+    ib.ib_sync_status()                      # the word was cleared
+    tr = ib.ib_forward(t, *args, w["dt"], 300)
+    ib.ib_sync_status()
+    assert torch.isfinite(tr).all()
