@@ -73,9 +73,9 @@ typedef struct {
 
 typedef struct {
     int32_t space_order;   /* M of the interior stencils: 2, 4, 6 or 8             */
-    int32_t basis_order;   /* order of the extrapolation basis; 0 -> M in 2D (the
-                              paper's consistent-error rule) and min(M, 4) in 3D
-                              (its order-reduction paragraph)                      */
+    int32_t basis_order;   /* order of the extrapolation basis; 0 -> min(M, 4)
+                              (the reduced basis of the order-reduction paragraph;
+                              M gives the consistent-error basis)                  */
     int32_t min_order;     /* lowest basis order of the fallback (>= 2)            */
     int32_t reserved;
     double radius;         /* initial support radius in grid units; <= 0 ->
@@ -86,9 +86,8 @@ typedef struct {
     double rank_tol;       /* full rank iff sigma_min > rank_tol * sigma_max       */
 } ib_opts;
 
-/* Fill `opts` with the defaults for space order M (basis 0: M in 2D, min(M, 4)
- * in 3D; min order 2, radius (basis+1)/2, growth 3, eta_p 0.5, eta_v 0,
- * rank_tol 1e-3). */
+/* Fill `opts` with the defaults for space order M (basis 0 = min(M, 4), min
+ * order 2, radius (basis+1)/2, growth 3, eta_p 0.5, eta_v 0, rank_tol 1e-3). */
 void ib_opts_default(ib_opts* opts, int32_t space_order);
 
 typedef struct ib_table ib_table;   /* opaque, library-owned */

@@ -759,7 +759,11 @@ __device__ void warp_solve_R(const double* R, const double* invd, int n, double*
     }
 }
 
-// sigma_min / sigma_max of R by power / inverse iteration in one warp (large n)
+// rank decisions whose first estimate lies in (tol, RANK_RECHECK tol] are
+// estimated again with RANK_ITERS_FINE iterations
+#define RANK_RECHECK 2.0
+#define RANK_ITERS_FINE 600
+
 // sigma_min / sigma_max of R by power and inverse iteration in one warp, in
 // FP32 (the rank decision needs a few digits; GB300's FP64 pipe is the
 // constructor's bottleneck).  x, y: scratch of n floats each.
@@ -769,14 +773,15 @@ __device__ float warp_norm_f(const float* x, int n) {
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     return sqrtf(s);
 }
-__device__ double warp_cond_ratio(const double* R, const double* invd, int n, double* xd, double* yd) {
+__device__ double warp_cond_ratio(const double* R, const double* invd, int n, double* xd, double* yd,
+                                  int it_max, int it_min) {
     const int lane = threadIdx.x & 31;
     float* x = (float*)xd;
     float* y = (float*)yd;
     for (int i = lane; i < n; i += 32) x[i] = rsqrtf((float)n);
     __syncwarp();
     float smax2 = 0.f;
-    for (int it = 0; it < 24; ++it) {
+    for (int it = 0; it < it_max; ++it) {
         for (int i = lane; i < n; i += 32) {
             float s = 0.f;
             for (int j = i; j < n; ++j) s += (float)R[i * n + j] * x[j];
@@ -801,7 +806,7 @@ __device__ double warp_cond_ratio(const double* R, const double* invd, int n, do
     for (int i = lane; i < n; i += 32) x[i] /= nx0;
     __syncwarp();
     float smin2 = 0.f;
-    for (int it = 0; it < 40; ++it) {
+    for (int it = 0; it < it_min; ++it) {
         // R^T w = x, then R x' = w (forward and back substitution, one warp)
         for (int k = 0; k < n; ++k) {
             const float wk = x[k] * (float)invd[k];
@@ -829,14 +834,15 @@ __device__ double warp_cond_ratio(const double* R, const double* invd, int n, do
 // The same estimate from an FP32 copy of R packed by rows (upper triangle):
 // element (i, j), j >= i, at rs(i) + j - i with rs(i) = i (2n - i + 1) / 2.
 __device__ __forceinline__ int packed_rs(int i, int n) { return i * (2 * n - i + 1) / 2; }
-__device__ double warp_cond_ratio_packed(const float* Rp, const float* invf, int n, double* xd, double* yd) {
+__device__ double warp_cond_ratio_packed(const float* Rp, const float* invf, int n, double* xd, double* yd,
+                                         int it_max, int it_min) {
     const int lane = threadIdx.x & 31;
     float* x = (float*)xd;
     float* y = (float*)yd;
     for (int i = lane; i < n; i += 32) x[i] = rsqrtf((float)n);
     __syncwarp();
     float smax2 = 0.f;
-    for (int it = 0; it < 24; ++it) {
+    for (int it = 0; it < it_max; ++it) {
         for (int i = lane; i < n; i += 32) {
             const float* row = Rp + packed_rs(i, n) - i;
             float s = 0.f;
@@ -866,7 +872,7 @@ __device__ double warp_cond_ratio_packed(const float* Rp, const float* invf, int
     for (int i = lane; i < n; i += 32) x[i] /= nx0;
     __syncwarp();
     float smin2 = 0.f;
-    for (int it = 0; it < 40; ++it) {
+    for (int it = 0; it < it_min; ++it) {
         for (int k = 0; k < n; ++k) {
             const float wk = x[k] * invf[k];
             __syncwarp();
@@ -1371,12 +1377,26 @@ __global__ void __launch_bounds__(FIT_THREADS) k_fit(FitParams P) {
                         float* fm = (float*)S.B;
                         for (int i = threadIdx.x; i < ncol * ncol; i += blockDim.x) fm[i] = (float)S.R[i];
                         __syncthreads();
-                        float smax = block_sigma_max(fm, ncol, fv, fv + ncm, S.scald + 4, 30);
-                        __syncthreads();
-                        for (int i = threadIdx.x; i < ncol * ncol; i += blockDim.x) fm[i] = (float)S.X[i];
-                        __syncthreads();
-                        float sinv = block_sigma_max(fm, ncol, fv, fv + ncm, S.scald + 4, 30);
-                        ratio = (smax > 0.f && sinv > 0.f && sinv < 3e38f) ? 1.0 / ((double)smax * (double)sinv) : 0.0;
+                        // Power iteration approaches each sigma_max from below, so the
+                        // estimated ratio is never below the true one: a fit it rejects is
+                        // rank deficient, and an acceptance close to the threshold is
+                        // checked again with RANK_ITERS_FINE iterations.
+                        for (int pass = 0; pass < 2; ++pass) {
+                            const int iters = pass ? RANK_ITERS_FINE : 30;
+                            if (pass) {
+                                for (int i = threadIdx.x; i < ncol * ncol; i += blockDim.x) fm[i] = (float)S.R[i];
+                                __syncthreads();
+                            }
+                            float smax = block_sigma_max(fm, ncol, fv, fv + ncm, S.scald + 4, iters);
+                            __syncthreads();
+                            for (int i = threadIdx.x; i < ncol * ncol; i += blockDim.x) fm[i] = (float)S.X[i];
+                            __syncthreads();
+                            float sinv = block_sigma_max(fm, ncol, fv, fv + ncm, S.scald + 4, iters);
+                            __syncthreads();
+                            ratio = (smax > 0.f && sinv > 0.f && sinv < 3e38f) ? 1.0 / ((double)smax * (double)sinv)
+                                                                               : 0.0;
+                            if (!(ratio > P.rank_tol && ratio < RANK_RECHECK * P.rank_tol)) break;
+                        }
                     } else {
                         // packed FP32 copy of R (and 1/R_kk) in the free panel buffer when it fits
                         const int npk = ncol * (ncol + 1) / 2;
@@ -1391,8 +1411,14 @@ __global__ void __launch_bounds__(FIT_THREADS) k_fit(FitParams P) {
                             __syncthreads();
                         }
                         if (threadIdx.x < 32) {
-                            double rr = packed ? warp_cond_ratio_packed(rp, rp + npk, ncol, S.vec, S.vec + ncm)
-                                               : warp_cond_ratio(S.R, S.invd, ncol, S.vec, S.vec + ncm);
+                            // the same one-sided estimate; near the threshold, again with more iterations
+                            double rr = 0.0;
+                            for (int pass = 0; pass < 2; ++pass) {
+                                const int im = pass ? RANK_ITERS_FINE : 24, in = pass ? RANK_ITERS_FINE : 40;
+                                rr = packed ? warp_cond_ratio_packed(rp, rp + npk, ncol, S.vec, S.vec + ncm, im, in)
+                                            : warp_cond_ratio(S.R, S.invd, ncol, S.vec, S.vec + ncm, im, in);
+                                if (!(rr > P.rank_tol && rr < RANK_RECHECK * P.rank_tol)) break;
+                            }
                             if (threadIdx.x == 0) S.scald[4] = rr;
                         }
                         __syncthreads();
@@ -1986,9 +2012,8 @@ static ib_status build_impl(const ib_grid* grid, const double* sdf, ib_bc bc, ib
         ib_set_error("space_order must be 2, 4, 6 or 8");
         return IB_ERR_ARG;
     }
-    // basis order M (consistent error, 3D expansion paragraph); in 3D reduced to 4
-    // at M > 4 (order-reduction paragraph: the order-8 footprint holds ~380 points)
-    if (o.basis_order <= 0) o.basis_order = grid->ndim == 2 ? M : std::min(M, 4);
+    // basis order min(M, 4): the order-reduction paragraph's reduced basis at M > 4
+    if (o.basis_order <= 0) o.basis_order = std::min(M, 4);
     if (o.basis_order > M || (o.basis_order & 1)) {
         ib_set_error("basis_order must be even and <= space_order");
         return IB_ERR_ARG;

@@ -272,8 +272,7 @@ class Mlp:
         cfg.n_hidden = int(n_hidden)
         cfg.n_layers = int(n_layers)
         cfg.in_radius = float(in_radius)
-        basis = space_order if ndim == 2 else min(space_order, 4)
-        cfg.out_radius = float(out_radius if out_radius is not None else (basis + 1) / 2.0)
+        cfg.out_radius = float(out_radius if out_radius is not None else (min(space_order, 4) + 1) / 2.0)
         self.cfg = cfg
         h = ctypes.c_void_p()
         _check(L.ib_mlp_create(ctypes.byref(cfg), ctypes.byref(h)))

@@ -70,5 +70,12 @@ def rel_l2(a, b):
 
 
 def record(name, **vals):
-    """Print a measured parity figure (collected from the test log to set tolerances)."""
-    print("PARITY %s %s" % (name, " ".join("%s=%.3e" % (k, v) for k, v in vals.items())), flush=True)
+    """Report a measured parity figure: printed, and appended to the file named by
+    the environment variable IB_PARITY_LOG when it is set."""
+    import os
+    line = "PARITY %s %s" % (name, " ".join("%s=%.3e" % (k, v) for k, v in vals.items()))
+    print(line, flush=True)
+    path = os.environ.get("IB_PARITY_LOG")
+    if path:
+        with open(path, "a") as f:
+            f.write(line + "\n")

@@ -66,7 +66,7 @@ def test_whole_field_order4(bc):
 
 @pytest.mark.parametrize("bc", ["free", "rigid"])
 def test_whole_field_order8_basis4(bc):
-    """Order-8 interior with the order-4 basis (the 3D default at M = 8): the
+    """Order-8 interior with the order-4 basis (the default at M = 8): the
     basis order bounds the convergence, >= 4 - 0.7 (measured 4.65 free, 3.55 rigid)."""
     o, e = _orders(8, 4, bc, (1 / 30, 1 / 90))
     assert all(x >= 4 - 0.7 for x in o), (o, e)
@@ -74,7 +74,7 @@ def test_whole_field_order8_basis4(bc):
 
 @pytest.mark.parametrize("bc,bound", [("free", 8 - 0.7), ("rigid", 8 - 1.5)])
 def test_whole_field_order8_basis8(bc, bound):
-    """Order-8 interior and basis (the 2D default at M = 8): free >= 8 - 0.7
+    """Order-8 interior and basis (ib_order = M): free >= 8 - 0.7
     (measured 8.39); rigid >= 8 - 1.5 (measured 7.39, then 6.69 on the next
     refinement: the rigid hierarchy imposes M/2 conditions per boundary
     point, the free one M/2 + 1)."""
