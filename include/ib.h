@@ -166,6 +166,22 @@ typedef struct {
     void* traces_dev;           /* [nrec][nt] output: trace[r][n] = p^{n+1} at r     */
     int32_t nsrc;               /* 0 .. 32 (more: IB_ERR_ARG)                       */
     int32_t nrec;
+    /* Absorbing layer along the side edges and the bottom (the paper's
+     * examples use zero Dirichlet edges and note that a damping boundary of
+     * choice combines with the method, Examples section).  The second-order
+     * form solves p_tt + eta(x) p_t = c^2 lap p + f there, eta = eta_max
+     * min(1, d^2 / W^2), d the node's distance (in nodes) into the layer of W
+     * = damp_width nodes: from x = 0 and x = nx-1 (and y = 0, y = ny-1 in
+     * 3D) and from the last z plane; the top carries the immersed boundary.
+     * The step is p^{n+1} = (2 p^n - (1 - a) p^{n-1} + dt^2 c^2 L p^n +
+     * dt^2 f) / (1 + a) with a = eta dt / 2.  damp_width = 0 or damp_eta = 0:
+     * no layer (zero Dirichlet edges).  Second-order form only (the
+     * first-order form and ib_forward_noalloc return IB_ERR_STATE); the
+     * adjoint is that of the damped map.  IB_ERR_ARG unless damp_eta >= 0 and
+     * 0 <= damp_width < nx / 2. */
+    double damp_eta;            /* eta_max (1/s)                                     */
+    int32_t damp_width;         /* W (nodes)                                         */
+    int32_t reserved;
 } ib_shot;
 
 /*
@@ -432,7 +448,8 @@ ib_status ib_sync_status(void* stream);
  * *growth the geometric-mean growth per step over the second half, an
  * estimate of the spectral radius of the one-step map (1 for a neutrally
  * stable scheme, > 1 when some mode grows).
- *   vel_dev, rho_dev  as in ib_shot (rho only for the first-order form).
+ *   shot              its vel_dev, rho_dev (first-order form) and absorbing
+ *                     layer are used; sources and receivers are ignored.
  *   precision         32 or 64;  dt the time step of the intended run.
  *   max_gain          IB_ERR_UNSTABLE (with *growth set) when
  *                     growth^n_steps > max_gain, i.e. an unstable mode would
@@ -440,9 +457,9 @@ ib_status ib_sync_status(void* stream);
  * Synchronises the stream.  Errors: IB_ERR_ARG, IB_ERR_STATE (first-order form
  * in 3D), IB_ERR_OOM, IB_ERR_CUDA, IB_ERR_UNSTABLE.
  */
-ib_status ib_stability(const ib_table* table, const void* vel_dev, const void* rho_dev,
-                       int32_t precision, double dt, int32_t n_steps, uint64_t seed,
-                       double max_gain, double* growth, void* stream);
+ib_status ib_stability(const ib_table* table, const ib_shot* shot, int32_t precision,
+                       double dt, int32_t n_steps, uint64_t seed, double max_gain,
+                       double* growth, void* stream);
 
 /* Thread-local message of the last failure ("" if none). */
 const char* ib_last_error(void);

@@ -10,10 +10,13 @@ from . import operators, propagate, stencils
 class Leapfrog:
     """Second-order form on one geometry: modified Laplacian, K, S, R."""
 
-    def __init__(self, sdf, vel, h, M, bc, dt, src, rec, opts=None):
+    def __init__(self, sdf, vel, h, M, bc, dt, src, rec, opts=None, damp=None):
+        """damp: None or (width in nodes, eta_max in 1/s) of the absorbing layer."""
         self.opts = opts or stencils.Opts(M)
         self.geom = stencils.Geometry(sdf, h, M)
         self.L, self.rows = operators.laplacian_matrix(self.geom, bc, self.opts)
+        self.a = (propagate.damping_coefficient(self.geom.sdf.shape, damp[0], damp[1], dt) * self.geom.mask.ravel()
+                  if damp is not None else None)
         self.vel = np.asarray(vel, dtype=np.float64)
         self.dt = dt
         self.h = h
@@ -25,7 +28,7 @@ class Leapfrog:
         self.R = propagate.multilinear_matrix(rec, h, shape, self.geom.mask)
 
     def forward(self, wavelet, nt, keep_history=False):
-        return propagate.forward_leapfrog(self.L, self.K, self.S, wavelet, self.R, nt, keep_history)
+        return propagate.forward_leapfrog(self.L, self.K, self.S, wavelet, self.R, nt, keep_history, self.a)
 
     def with_velocity(self, vel):
         out = object.__new__(Leapfrog)
@@ -36,7 +39,7 @@ class Leapfrog:
 
     def adjoint(self, residual, hist):
         return propagate.adjoint_leapfrog(self.L, self.K, self.vel.reshape(-1), self.dt, self.R,
-                                          residual, self.S, hist)
+                                          residual, self.S, hist, self.a)
 
 
 class Staggered:

@@ -53,12 +53,13 @@ def growth_from_mu(mu):
     return float(max(np.abs(l1).max(), np.abs(l2).max()))
 
 
-def leapfrog_growth(L, K, nsteps=2000, seed=0, renorm=50):
+def leapfrog_growth(L, K, nsteps=2000, seed=0, renorm=50, a=None):
     """Power iteration on the leapfrog companion map.  Starts from a seeded
     random p^0 = p^{-1} on interior nodes, steps source-free, renormalises every
     `renorm` steps, and returns (rho estimate, log-norm history).  For a
     stable scheme the estimate tends to 1; an unstable mode with |lambda| = rho
-    dominates once rho^n outgrows the initial transient."""
+    dominates once rho^n outgrows the initial transient.  a: absorbing-layer
+    coefficient per node (``propagate.damping_coefficient``) or None."""
     K = np.asarray(K, dtype=np.float64)
     rng = np.random.default_rng(seed)
     p = rng.standard_normal(K.shape[0]) * (K != 0.0)
@@ -67,7 +68,10 @@ def leapfrog_growth(L, K, nsteps=2000, seed=0, renorm=50):
     scale = 0.0
     logn[0] = np.log(np.sqrt(np.dot(p, p) + np.dot(pm, pm)))
     for n in range(1, nsteps + 1):
-        pn = 2.0 * p - pm + K * (L @ p)
+        if a is None:
+            pn = 2.0 * p - pm + K * (L @ p)
+        else:
+            pn = (2.0 * p - (1.0 - a) * pm + K * (L @ p)) / (1.0 + a)
         pm, p = p, pn
         nrm = np.sqrt(np.dot(p, p) + np.dot(pm, pm))
         logn[n] = scale + np.log(nrm)

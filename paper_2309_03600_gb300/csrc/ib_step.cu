@@ -193,7 +193,32 @@ struct StepArgs {
     T* buf1;
     int64_t ntx;         // tiles along x
     int64_t ntiles;      // tiles of the shot (blocks beyond only record receivers)
+    int dw;              // absorbing layer width in nodes (0: none)
+    T da;                // its largest a = eta_max dt / 2
 };
+
+// Absorbing layer along the side edges and the bottom (not the top, where the
+// immersed boundary is): a = a_max min(1, d^2 / W^2) with d the node's distance
+// into the layer of W nodes, d^2 = dx^2 (+ dy^2) + dz^2, dz counted from the
+// bottom only.  The damped leapfrog step of p_tt + 2 a / dt p_t = c^2 lap p + f,
+//   p^{n+1} = (2 p^n - (1 - a) p^{n-1} + dt^2 c^2 L p^n + dt^2 f) / (1 + a),
+// is the undamped update u followed by u - g (u - p^{n-1}) with g = a / (1 + a).
+template <typename T>
+__device__ __forceinline__ T damp_a(const Layout& L, int dw, T da, int64_t x, int64_t y, int64_t z) {
+    const int64_t w = dw;
+    const int64_t dx = max(max(w - x, x - (L.nx - 1 - w)), (int64_t)0);
+    const int64_t dy = L.ndim == 3 ? max(max(w - y, y - (L.ny - 1 - w)), (int64_t)0) : 0;
+    const int64_t dz = max(z - (L.nz - 1 - w), (int64_t)0);
+    const int64_t d2 = dx * dx + dy * dy + dz * dz;
+    if (d2 == 0) return (T)0;
+    const T r = (T)d2 / (T)(w * w);
+    return da * (r < (T)1 ? r : (T)1);
+}
+template <typename T>
+__device__ __forceinline__ T damp_g(const Layout& L, int dw, T da, int64_t x, int64_t y, int64_t z) {
+    const T av = damp_a<T>(L, dw, da, x, y, z);
+    return av / ((T)1 + av);
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -265,7 +290,9 @@ __device__ __forceinline__ void leap2d_tile(const StepArgs<T>& a, int64_t bx, in
         if (x0 + lx >= L.nx || z0 + lz >= L.nz) continue;
         const int64_t q = origin + lz * L.px + lx;
         const T c = tile[lz + H][lx + H];
-        a.out[q] = c + ((c - pmv[j]) + khv[j] * acc[i]) + sadd[i];
+        T u = c + ((c - pmv[j]) + khv[j] * acc[i]) + sadd[i];
+        if (a.dw) u -= damp_g<T>(L, a.dw, a.da, x0 + lx, 0, z0 + lz) * (u - pmv[j]);
+        a.out[q] = u;
     }
 }
 
@@ -468,7 +495,9 @@ __device__ __forceinline__ void leap2d_strip(const StepArgs<float>& a, int64_t b
             const int i = i0 + j * TX;
             if (xin && s * TZ + j < zleft) {
                 const float c = cv[j];
-                outp[j * L.px] = c + ((c - pmS[i]) + khS[i] * sm.acc[i]) + sm.sadd[i];
+                float u = c + ((c - pmS[i]) + khS[i] * sm.acc[i]) + sm.sadd[i];
+                if (a.dw) u -= damp_g<float>(L, a.dw, a.da, x0 + lx, 0, zs + s * TZ + lz0 + j) * (u - pmS[i]);
+                outp[j * L.px] = u;
             }
             sm.sadd[i] = 0.f;
         }
@@ -629,7 +658,10 @@ __global__ void __launch_bounds__(256) k_leap3d(StepArgs<T> a, int zchunk, int64
         if (valid) {
             int64_t qi = L.idx(x, y, z);
             T c = q[H];
-            a.out[qi] = c + ((c - a.pm[qi]) + a.Kh[qi] * acc[tid]) + sadd[tid];
+            const T pmq = a.pm[qi];
+            T u = c + ((c - pmq) + a.Kh[qi] * acc[tid]) + sadd[tid];
+            if (a.dw) u -= damp_g<T>(L, a.dw, a.da, x, y, z) * (u - pmq);
+            a.out[qi] = u;
         }
 #pragma unroll
         for (int k = 0; k < 2 * H; ++k) q[k] = q[k + 1];
@@ -832,7 +864,9 @@ __global__ void __launch_bounds__(256) k_leap3d_tma(StepArgs<float> a, const __g
         __syncthreads();
         if (valid) {
             const float c = q[H];
-            a.out[qc] = c + ((c - pm_c) + kh_c * acc[tid]) + sadd[tid];
+            float u = c + ((c - pm_c) + kh_c * acc[tid]) + sadd[tid];
+            if (a.dw) u -= damp_g<float>(L, a.dw, a.da, x, y, z) * (u - pm_c);
+            a.out[qc] = u;
         }
 #pragma unroll
         for (int k = 0; k < 2 * H; ++k) q[k] = q[k + 1];
@@ -1195,6 +1229,8 @@ struct AdjArgs {
     PointSet<T> src;
     const T* wavelet;
     T* gw;               // [nt] or null
+    int dw;              // absorbing layer (as StepArgs); the stored multiplier is
+    T da;                // nu^m = mu^m / (1 + a)
 };
 
 // one adjoint tile (bx, bz); shared arrays from the calling kernel
@@ -1301,11 +1337,18 @@ __device__ __forceinline__ void adj2d_tile(const AdjArgs<T>& a, int64_t bx, int6
         const int i = tid + 256 * j, lz = i / TX, lx = i - lz * TX;
         if (x0 + lx >= L.nx || z0 + lz >= L.nz) continue;
         const int64_t q = origin + lz * L.px + lx;
-        const T mu_new = (T)2 * mu_v[j] - mum_v[j] + acc[i];
+        // With an absorbing layer the buffers hold nu = mu / (1 + a): the transpose of
+        // p^{n+1} = ((2 + K L) p^n - (1 - a) p^{n-1} + s) / (1 + a) is
+        // mu^m = 2 nu^{m+1} - (1 - a) nu^{m+2} + L^T (K nu^{m+1}) + R^T res^{m-1}.
+        const T av = a.dw ? damp_a<T>(L, a.dw, a.da, x0 + lx, 0, z0 + lz) : (T)0;
+        T mu_new = (T)2 * mu_v[j] - ((T)1 - av) * mum_v[j] + acc[i];
+        if (a.dw) mu_new = mu_new / ((T)1 + av);
         a.out[q] = mu_new;
         const T Kq = kh_v[j];
         if (Kq > (T)0) {
+            // dt^2 c^2 (L p^{m-1}) = (1 + a) p^m - 2 p^{m-1} + (1 - a) p^{m-2} - s^{m-1}
             T d2 = (p0_v[j] - p1_v[j]) - (p1_v[j] - p2_v[j]);
+            if (a.dw) d2 += av * (p0_v[j] - p2_v[j]);
             const T srcw = sw[i];
             d2 -= srcw * wv;
             a.grad[q] = g_v[j] + mu_new * (a.two_dt_over_h / sqrt(Kq)) * d2;
@@ -1639,6 +1682,8 @@ static ib_status make_plane_map(CUtensorMap& tm, void* base, const Layout& L) {
     return IB_OK;
 }
 
+static bool shot_damped(const ib_shot* sh) { return sh->damp_width > 0 && sh->damp_eta > 0.0; }
+
 static ib_status check_shot(const ib_table* t, const ib_shot* sh, int precision, double dt, int nt,
                             bool need_traces = true) {
     if (!t || !sh) {
@@ -1658,6 +1703,11 @@ static ib_status check_shot(const ib_table* t, const ib_shot* sh, int precision,
         ib_set_error("missing shot arrays");
         return IB_ERR_ARG;
     }
+    if (!(sh->damp_eta >= 0.0) || sh->damp_width < 0 ||
+        (shot_damped(sh) && 2 * (int64_t)sh->damp_width >= t->grid.n[0])) {
+        ib_set_error("absorbing layer: damp_eta >= 0 and 0 <= damp_width < nx / 2 required");
+        return IB_ERR_ARG;
+    }
     if (sh->nsrc > 32) {
         // the step kernels spread each source over its 8 interpolation corners with
         // one thread per corner of a 256-thread block
@@ -1671,6 +1721,13 @@ template <typename T>
 struct Geom {
     PointSet<T> src, rec;
 };
+
+// absorbing layer of a shot: width and a_max = eta_max dt / 2 (formed in FP64)
+template <typename T>
+static void set_damping(const ib_shot* sh, double dt, int& dw, T& da) {
+    dw = shot_damped(sh) ? sh->damp_width : 0;
+    da = dw ? (T)(0.5 * sh->damp_eta * dt) : (T)0;
+}
 
 template <typename T>
 static ib_status setup_points(const ib_table* t, const ib_shot* sh, double scale, Scratch& S, Geom<T>& g) {
@@ -1779,6 +1836,7 @@ static ib_status forward_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, 
     a.rec = g.rec;
     a.traces = (T*)sh->traces_dev;
     a.nt = nt;
+    set_damping<T>(sh, dt, a.dw, a.da);
     const int64_t seg = ckpt ? ckpt_seg(nt, n_ckpt) : 0;
     T* cur = p0;   // p^n
     T* prev = p1;  // p^{n-1}
@@ -2066,6 +2124,10 @@ static ib_status forward_stag(ib_table* t, const ib_shot* sh, double dt, int nt,
                               const Probe* probe = nullptr) {
     const Layout& L = t->L;
     const int d = t->grid.ndim;
+    if (shot_damped(sh)) {
+        ib_set_error("the absorbing layer is implemented for the second-order form");
+        return IB_ERR_STATE;
+    }
     if (d != 2) {
         ib_set_error("the staggered form is implemented in 2D");
         return IB_ERR_STATE;
@@ -2345,6 +2407,7 @@ static ib_status adjoint_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, 
     fa.rec.n = 0;
     fa.rec_step = -1;
     fa.nt = nt;
+    set_damping<T>(sh, dt, fa.dw, fa.da);
     AdjArgs<T> aa;
     memset(&aa, 0, sizeof aa);
     aa.L = L;
@@ -2362,6 +2425,7 @@ static ib_status adjoint_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, 
     aa.src = g.src;
     aa.wavelet = (const T*)sh->wavelet_dev;
     aa.gw = gw;
+    set_damping<T>(sh, dt, aa.dw, aa.da);
     dim3 grid2((unsigned)((L.nx + TX2 - 1) / TX2), (unsigned)((L.nz + TZ2 - 1) / TZ2));
     T* mu_a = mu1;   // mu^{m+1}
     T* mu_b = mu2;   // mu^{m+2}
@@ -2520,6 +2584,7 @@ static ib_status batch_prepare(ib_table* const* ts, const ib_shot* shots, int ns
         a.nt = nt;
         a.buf0 = buf0[i];
         a.buf1 = buf1[i];
+        set_damping<float>(&shots[i], dt, a.dw, a.da);
         a.ntx = (L.nx + tx - 1) / tx;
         const int nsub = kShapes[si].nsub;
         int64_t ntiles = a.ntx * ((((L.nz + tz - 1) / tz) + nsub - 1) / nsub);
@@ -2824,6 +2889,7 @@ extern "C" ib_status ib_adjoint_batch(const ib_table* const* tables, const ib_sh
         fa.rec.n = 0;
         fa.rec_step = -1;
         fa.nt = nt;
+        set_damping<float>(&shots[i], dt, fa.dw, fa.da);
         fa.buf0 = segbuf;
         fa.ntx = (L.nx + TX2 - 1) / TX2;
         fa.ntiles = fa.ntx * ((L.nz + TZ2 - 1) / TZ2);
@@ -2844,6 +2910,7 @@ extern "C" ib_status ib_adjoint_batch(const ib_table* const* tables, const ib_sh
         aa.src = g.src;
         aa.wavelet = (const float*)shots[i].wavelet_dev;
         aa.gw = nullptr;
+        set_damping<float>(&shots[i], dt, aa.dw, aa.da);
         aargs[i].mu1 = mu1;
         aargs[i].mu2 = mu2;
         aargs[i].seg = segbuf;
@@ -2974,13 +3041,12 @@ extern "C" ib_status ib_sync_status(void* stream) {
     return IB_OK;
 }
 
-extern "C" ib_status ib_stability(const ib_table* tc, const void* vel_dev, const void* rho_dev, int32_t precision,
-                                  double dt, int32_t n_steps, uint64_t seed, double max_gain, double* growth,
-                                  void* stream) {
+extern "C" ib_status ib_stability(const ib_table* tc, const ib_shot* shot, int32_t precision, double dt,
+                                  int32_t n_steps, uint64_t seed, double max_gain, double* growth, void* stream) {
     ib_set_error("");
-    if (!tc || !vel_dev || !growth || (precision != 32 && precision != 64) || !(dt > 0.0) || n_steps < 1 ||
-        !(max_gain > 1.0)) {
-        ib_set_error("ib_stability: table, velocity and output required; precision 32 or 64, dt > 0, "
+    if (!tc || !shot || !shot->vel_dev || !growth || (precision != 32 && precision != 64) || !(dt > 0.0) ||
+        n_steps < 1 || !(max_gain > 1.0)) {
+        ib_set_error("ib_stability: table, shot with velocity and output required; precision 32 or 64, dt > 0, "
                      "n_steps >= 1, max_gain > 1");
         return IB_ERR_ARG;
     }
@@ -3001,8 +3067,11 @@ extern "C" ib_status ib_stability(const ib_table* tc, const void* vel_dev, const
     TRY(S.alloc(&pr.logs, pr.nslot, true));
     ib_shot sh;
     memset(&sh, 0, sizeof sh);
-    sh.vel_dev = vel_dev;
-    sh.rho_dev = rho_dev;
+    sh.vel_dev = shot->vel_dev;
+    sh.rho_dev = shot->rho_dev;
+    sh.damp_eta = shot->damp_eta;
+    sh.damp_width = shot->damp_width;
+    TRY(check_shot(tc, &sh, precision, dt, n_steps));
     if (t->form == IB_SECOND_ORDER)
         TRY(precision == 64 ? forward_2nd<double>(t, &sh, dt, nt, nullptr, 0, s, &pr)
                             : forward_2nd<float>(t, &sh, dt, nt, nullptr, 0, s, &pr));
@@ -3094,6 +3163,10 @@ extern "C" ib_status ib_forward_noalloc(const ib_table* tc, const ib_shot* sh, d
     ib_table* t = const_cast<ib_table*>(tc);
     if (t->form != IB_SECOND_ORDER || t->grid.ndim != 2) {
         ib_set_error("ib_forward_noalloc: 2D second-order tables only");
+        return IB_ERR_STATE;
+    }
+    if (shot_damped(sh)) {
+        ib_set_error("ib_forward_noalloc: no absorbing layer");
         return IB_ERR_STATE;
     }
     const Layout& L = t->L;

@@ -64,7 +64,8 @@ class Shot(ctypes.Structure):
     _fields_ = [("vel_dev", ctypes.c_void_p), ("rho_dev", ctypes.c_void_p),
                 ("src_dev", ctypes.c_void_p), ("rec_dev", ctypes.c_void_p),
                 ("wavelet_dev", ctypes.c_void_p), ("traces_dev", ctypes.c_void_p),
-                ("nsrc", ctypes.c_int32), ("nrec", ctypes.c_int32)]
+                ("nsrc", ctypes.c_int32), ("nrec", ctypes.c_int32),
+                ("damp_eta", ctypes.c_double), ("damp_width", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 _LIB = None
@@ -146,7 +147,7 @@ def load(path=LIB_PATH):
     L.ib_build_stencils_learned.restype = i32
     L.ib_table_learned.argtypes = [vp, ctypes.POINTER(i64), ctypes.POINTER(i64), vp]
     L.ib_table_learned.restype = i32
-    L.ib_stability.argtypes = [vp, vp, vp, i32, dbl, i32, ctypes.c_uint64, dbl, ctypes.POINTER(dbl), vp]
+    L.ib_stability.argtypes = [vp, ctypes.POINTER(Shot), i32, dbl, i32, ctypes.c_uint64, dbl, ctypes.POINTER(dbl), vp]
     L.ib_stability.restype = i32
     _LIB = L
     return L
@@ -373,8 +374,12 @@ def ib_table_export(table, op):
     return dict(row_node=row_node[:nr], row_ptr=row_ptr, col=col[:nz], w=w[:nz], info=info[:nr])
 
 
-def _shot(vel, rho, src, rec, wavelet, traces):
+def _shot(vel, rho, src, rec, wavelet, traces, damp=None):
+    """damp: None or (width in nodes, eta_max in 1/s) of the absorbing layer."""
     s = Shot()
+    if damp is not None:
+        s.damp_width = int(damp[0])
+        s.damp_eta = float(damp[1])
     s.vel_dev = vel.data_ptr()
     s.rho_dev = rho.data_ptr() if rho is not None else None
     s.src_dev = src.data_ptr() if src is not None and src.numel() else None
@@ -395,25 +400,26 @@ def ib_checkpoint_bytes(table, precision, nt, n_ckpt):
 
 
 def ib_forward(table, vel, wavelet, src, rec, dt, nt, rho=None, ckpt=None, n_ckpt=0, traces=None,
-               stream=None):
+               damp=None, stream=None):
     """vel, rho, wavelet: CUDA tensors of one float dtype (its precision is used);
-    src, rec: CUDA float64 [n][ndim] metres.  Returns traces [nrec][nt]."""
+    src, rec: CUDA float64 [n][ndim] metres; damp: None or (width, eta_max) of
+    the absorbing layer.  Returns traces [nrec][nt]."""
     for t in (vel, wavelet):
         assert t.is_cuda and t.is_contiguous()
     if traces is None:
         traces = torch.zeros((rec.shape[0], nt), dtype=vel.dtype, device=vel.device)
-    sh = _shot(vel, rho, src, rec, wavelet, traces)
+    sh = _shot(vel, rho, src, rec, wavelet, traces, damp)
     _check(load().ib_forward(table.handle, ctypes.byref(sh), _prec(vel.dtype), float(dt), int(nt),
                              _ptr(ckpt), int(n_ckpt), _stream(stream)))
     return traces
 
 
 def ib_adjoint(table, vel, wavelet, src, rec, dt, nt, ckpt, n_ckpt, residual, want_wavelet_grad=False,
-               stream=None):
+               damp=None, stream=None):
     """Returns (dJ/dvel [same shape as vel], dJ/dwavelet [nt] or None)."""
     grad = torch.zeros_like(vel)
     gw = torch.zeros(nt, dtype=vel.dtype, device=vel.device) if want_wavelet_grad else None
-    sh = _shot(vel, None, src, rec, wavelet, None)
+    sh = _shot(vel, None, src, rec, wavelet, None, damp)
     _check(load().ib_adjoint(table.handle, ctypes.byref(sh), _prec(vel.dtype), float(dt), int(nt),
                              _ptr(ckpt), int(n_ckpt), _ptr(residual.contiguous()), _ptr(grad), _ptr(gw),
                              _stream(stream)))
@@ -439,7 +445,7 @@ def ib_forward_batch(tables, shots, dt, nt, stream=None):
         if tr is None:
             tr = torch.zeros((d["rec"].shape[0], nt), dtype=d["vel"].dtype, device=d["vel"].device)
         outs.append(tr)
-        sh[i] = _shot(d["vel"], d.get("rho"), d["src"], d["rec"], d["wavelet"], tr)
+        sh[i] = _shot(d["vel"], d.get("rho"), d["src"], d["rec"], d["wavelet"], tr, d.get("damp"))
     _check(load().ib_forward_batch(arr, sh, n, 32, float(dt), int(nt), _stream(stream)))
     return outs
 
@@ -454,7 +460,7 @@ def _batch_shots(tables, shots, nt, need_traces=True):
         if tr is None and need_traces:
             tr = torch.zeros((d["rec"].shape[0], nt), dtype=d["vel"].dtype, device=d["vel"].device)
         outs.append(tr)
-        sh[i] = _shot(d["vel"], d.get("rho"), d["src"], d["rec"], d["wavelet"], tr)
+        sh[i] = _shot(d["vel"], d.get("rho"), d["src"], d["rec"], d["wavelet"], tr, d.get("damp"))
     return n, arr, sh, outs
 
 
@@ -486,11 +492,12 @@ def ib_selftest_bounded_wait(stream=None):
     return load().ib_selftest_bounded_wait(_stream(stream))
 
 
-def ib_stability(table, vel, dt, n_steps, rho=None, seed=1, max_gain=100.0, stream=None):
+def ib_stability(table, vel, dt, n_steps, rho=None, seed=1, max_gain=100.0, damp=None, stream=None):
     """(per-step growth estimate, status): power iteration of the time stepping
     with the table's operators; status IB_ERR_UNSTABLE when growth^n_steps > max_gain."""
     g = ctypes.c_double(0.0)
-    st = load().ib_stability(table.handle, _ptr(vel), _ptr(rho), _prec(vel.dtype), float(dt), int(n_steps),
+    sh = _shot(vel, rho, None, None, None, None, damp)
+    st = load().ib_stability(table.handle, ctypes.byref(sh), _prec(vel.dtype), float(dt), int(n_steps),
                              int(seed), float(max_gain), ctypes.byref(g), _stream(stream))
     _check(st, allow=(IB_ERR_UNSTABLE,))
     return g.value, st

@@ -306,10 +306,18 @@ def workload_hills3d(nx=512, ny=512, nz=384, h=10.0, M=8, nt=2000, courant=0.45,
                 nt=nt, src=src, rec=rec, wavelet=ricker(f0, dt, nt), bc=bc, zsurf=zsurf)
 
 
+def damping_eta(cmax, width, h, reflection):
+    """Peak coefficient (1/s) of a quadratic absorbing layer of `width` nodes
+    for a nominal reflection coefficient: 1.5 cmax ln(1 / R) / (W h)."""
+    return 1.5 * cmax * math.log(1.0 / reflection) / (width * h)
+
+
 def workload_shot2d(shot, h=10.0, M=8, nt=2000, courant=0.4, f0=10.0, bc="free",
                     side=(400, 1200), device="cpu"):
     """One shot of the batched set: sides uniform in [400, 1200] (seed 4 + shot),
-    surface a + b sin(2 pi x / lam) + Gaussian bump, 3-5 layers below it."""
+    surface a + b sin(2 pi x / lam) + Gaussian bump, 3-5 layers below it; an
+    absorbing layer of 20 nodes on the sides and the bottom (nominal
+    reflection 1e-8) in `damp`."""
     rng = np.random.default_rng(4 + shot)
     nx = int(rng.integers(side[0], side[1] + 1))
     nz = int(rng.integers(side[0], side[1] + 1))
@@ -336,7 +344,8 @@ def workload_shot2d(shot, h=10.0, M=8, nt=2000, courant=0.4, f0=10.0, bc="free",
     rz = zs(xt).numpy() + 2 * h
     rec = np.stack([rx, rz], axis=1)
     return dict(name="shot2d_%d" % shot, ndim=2, shape=(nx, nz), h=h, M=M, sdf=sdf, vel=vel,
-                dt=dt, nt=nt, src=src, rec=rec, wavelet=ricker(f0, dt, nt), bc=bc)
+                dt=dt, nt=nt, src=src, rec=rec, wavelet=ricker(f0, dt, nt), bc=bc,
+                damp=(20, damping_eta(4000.0, 20, h, 1e-8)))
 
 
 # ---------------------------------------------------------------------------

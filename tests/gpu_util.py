@@ -4,6 +4,7 @@ import numpy as np
 import torch
 
 from oracle import sim, stencils
+from paper_2309_03600_gb300 import inputs
 
 
 def lin_to_node(lin, shape):
@@ -79,3 +80,11 @@ def record(name, **vals):
     if path:
         with open(path, "a") as f:
             f.write(line + "\n")
+
+
+def small_hills(nx=40, ny=36, nz=34, h=10.0, seed=13):
+    """A small seeded Gaussian-hills surface (3D parity cases)."""
+    prm = inputs.hills_params(5, seed, (nx - 1) * h, (ny - 1) * h, hmin=20, hmax=90, smin=60, smax=160)
+    parts = inputs.hills_surface(prm, datum=160.0, zmin=30.0)
+    sdf, zs = inputs.heightfield_sdf_3d(nx, ny, nz, h, parts)
+    return sdf, zs

@@ -7,14 +7,17 @@ import torch
 
 from oracle import sim, stencils
 from paper_2309_03600_gb300 import inputs
-from gpu_util import compare_tables, cuda, gpu_rows, record, rel_l2
+from gpu_util import compare_tables, cuda, gpu_rows, record, rel_l2, small_hills
 
 # FP64 traces: the library's weights come from its own FP64 factorisation
 # (Cholesky factor of the streamed Gram matrix, seminormal equations + one
-# refinement) of the same
-# A that the oracle pseudo-inverts by SVD; the two agree to ~1e-13 cond(A)
-# (table tests), which bounds the FP64 trace difference well below 1e-7.
-TOL64 = 1e-7
+# refinement) of the same A that the oracle pseudo-inverts by SVD.  Measured
+# FP64 trace differences on the GB300 are 3e-15 .. 1.5e-13 (second-order 2D
+# and 3D, staggered, many sources and receivers): the bound is about ten
+# times the largest.
+TOL64 = 1e-12
+# FP64 adjoint: measured 4e-15 (gradient) and 2e-14 (wavelet gradient).
+TOL64_ADJ = 2e-13
 # FP32 traces: the target relative L2 of the method's FP32 propagation.
 TOL32 = 1e-5
 
@@ -27,13 +30,6 @@ def circle_sdf(nx, nz, cx, cz, R, h=1.0):
     x = np.arange(nx)[None, :] - cx
     z = np.arange(nz)[:, None] - cz
     return (np.sqrt(x * x + z * z) - R) * h
-
-
-def small_hills(nx=40, ny=36, nz=34, h=10.0, seed=13):
-    prm = inputs.hills_params(5, seed, (nx - 1) * h, (ny - 1) * h, hmin=20, hmax=90, smin=60, smax=160)
-    parts = inputs.hills_surface(prm, datum=160.0, zmin=30.0)
-    sdf, zs = inputs.heightfield_sdf_3d(nx, ny, nz, h, parts)
-    return sdf, zs
 
 
 # ---------------------------------------------------------------------------
@@ -235,8 +231,8 @@ def test_adjoint_vs_oracle(bc, n_ckpt):
     ib.ib_sync_status()
     eg, ew = rel_l2(g.cpu().numpy().ravel(), g_ref), rel_l2(gw.cpu().numpy(), gw_ref)
     record("adjoint64_%s_ck%d" % (bc, n_ckpt), grad=eg, wavelet=ew)
-    assert eg < TOL64
-    assert ew < TOL64
+    assert eg < TOL64_ADJ
+    assert ew < TOL64_ADJ
 
 
 def test_adjoint_dot_product_fp32():
@@ -273,7 +269,7 @@ def test_autograd_function():
     g_ref, _ = s.adjoint(ref_tr, hist)
     e = rel_l2(v.grad.detach().cpu().numpy().ravel(), g_ref)
     record("autograd64", grad=e)
-    assert e < TOL64
+    assert e < TOL64_ADJ
 
 
 # ---------------------------------------------------------------------------
