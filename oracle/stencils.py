@@ -44,6 +44,13 @@ Readings of the paper used here (the paper is silent or ambiguous):
   steps; at 1e-3 it stays bounded over 1500 steps (2D unchanged);
 * expansion point: the stencil centre (2nd-order form); the node receiving the
   derivative (staggered form);
+* eta of the pressure fits: 0.5 for the free surface, as the paper sets it
+  (2D example-geometry paragraph), and 0.25 for the rigid surface, for which
+  the paper gives no value.  With 0.5 the rigid second-order scheme has a
+  growing mode on the seeded Gaussian hills (growth per step 1.10 on a
+  34 x 34 x 30 crop, 1.076 on the 512 x 512 x 384 model) and on the seeded
+  sinusoid (1.0021); with 0.25 the growth is 1.0004 and 1.00015.  Larger eta
+  makes it worse (0.75: 1.17, 1.0: 1.52 on the crop);
 * basis order of the extrapolants (``Opts.basis``): min(M, 4) by default.
   The paper asks for a basis of the interior order for consistent error (3D
   expansion paragraph of "Constructing Finite-Difference Approximations") and
@@ -71,17 +78,26 @@ class RankError(RuntimeError):
 
 
 class Opts:
-    def __init__(self, M, eta_p=0.5, eta_v=0.0, radius=0.0, growth=3.0,
+    def __init__(self, M, eta_p=None, eta_v=0.0, radius=0.0, growth=3.0,
                  min_order=2, rank_tol=1e-3, ib_order=0):
         self.M = int(M)
         # basis order of the extrapolants (<= M); 0 selects min(M, 4) (see basis)
         self.ib_order = int(ib_order)
-        self.eta_p = float(eta_p)
+        # pressure cut-off; None selects the default of eta_pressure(bc)
+        self.eta_p = None if eta_p is None else float(eta_p)
         self.eta_v = float(eta_v)
         self.radius = float(radius)
         self.growth = float(growth)
         self.min_order = int(min_order)
         self.rank_tol = float(rank_tol)
+
+    def eta_pressure(self, bc):
+        """eta of the pressure fits: eta_p if set, else 0.5 for the free surface
+        (the paper's value) and 0.25 for the rigid surface (the paper gives none;
+        see the module notes)."""
+        if self.eta_p is not None:
+            return self.eta_p
+        return 0.5 if bc == "free" else 0.25
 
     def basis(self, d):
         """Basis order of the extrapolants (d dimensions): ib_order if set, else min(M, 4)."""
@@ -272,7 +288,7 @@ def laplacian_rows(geom, bc, opts, nodes=None):
     M = opts.M
     w2 = [float(x) for x in taylor.central_second(M)]
     H = M // 2
-    fields = [Field(geom.mask, np.zeros(geom.d), opts.eta_p)]
+    fields = [Field(geom.mask, np.zeros(geom.d), opts.eta_pressure(bc))]
     bcfn = scalar_bc_fn(bc, geom.d)
     if nodes is None:
         nodes = laplacian_ib_nodes(geom.mask, M)
@@ -332,7 +348,7 @@ def gradient_rows(geom, a, bc, opts, nodes=None):
     """
     M = opts.M
     c = [float(x) for x in taylor.staggered_first(M)]      # at offsets -(M-1)/2..(M-1)/2
-    fields = [Field(geom.mask, np.zeros(geom.d), opts.eta_p)]
+    fields = [Field(geom.mask, np.zeros(geom.d), opts.eta_pressure(bc))]
     bcfn = scalar_bc_fn(bc, geom.d)
     if nodes is None:
         nodes = gradient_ib_nodes(geom, a, M)

@@ -96,7 +96,7 @@ extern "C" void ib_opts_default(ib_opts* o, int32_t M) {
     o->min_order = 2;
     o->radius = 0.0;
     o->growth = 3.0;
-    o->eta_p = 0.5;
+    o->eta_p = -1.0;   // by boundary condition: 0.5 free, 0.25 rigid
     o->eta_v = 0.0;
     o->rank_tol = 1e-3;
 }
@@ -2021,6 +2021,9 @@ static ib_status build_impl(const ib_grid* grid, const double* sdf, ib_bc bc, ib
     if (o.min_order < 2 || o.min_order > o.basis_order) o.min_order = std::min(2, o.basis_order);
     if (!(o.growth >= 0.0) || o.growth > 8.0) o.growth = 3.0;
     if (!(o.rank_tol > 0.0)) o.rank_tol = 1e-3;
+    // pressure cut-off: the paper's 0.5 for the free surface; 0.25 for the rigid
+    // surface, for which the paper gives none (0.5 leaves a growing mode there)
+    if (o.eta_p < 0.0) o.eta_p = bc == IB_RIGID ? 0.25 : 0.5;
     if (bc != IB_FREE && bc != IB_RIGID) {
         ib_set_error("bc must be IB_FREE or IB_RIGID");
         return IB_ERR_ARG;

@@ -915,6 +915,7 @@ struct StagPlan {
     const int32_t* rpb;      // pid range of the row
     const int32_t* rpe;
     const T* in;
+    int64_t n_in;            // partial sums in `in`
 };
 
 template <typename T>
@@ -1603,13 +1604,22 @@ struct Probe {
     double* logs;       // [nslot]
 };
 
+// Renormalise the state (a, b, c) by its norm; `extra` (n_extra values, not part
+// of the norm) holds quantities linear in the state that the next step reads --
+// the staggered form's producer-side partial sums -- and is scaled alike.
 template <typename T>
-static ib_status probe_rescale(const Probe* pr, int slot, int64_t n, T* a, T* b, T* c, cudaStream_t s) {
+static ib_status probe_rescale(const Probe* pr, int slot, int64_t n, T* a, T* b, T* c, cudaStream_t s,
+                               T* extra = nullptr, int64_t n_extra = 0) {
     k_sumsq<T><<<grid1(n, 256), 256, 0, s>>>(n, a, b, c, pr->sums + slot);
     k_rescale<T><<<grid1(n, 256), 256, 0, s>>>(n, a, b, c, pr->sums + slot, pr->logs + slot);
+    ib_count_launch("setup");
+    ib_count_launch("setup");
+    if (extra && n_extra > 0) {
+        k_rescale<T><<<grid1(n_extra, 256), 256, 0, s>>>(n_extra, extra, (T*)nullptr, (T*)nullptr,
+                                                          pr->sums + slot, pr->logs + slot);
+        ib_count_launch("setup");
+    }
     IB_CHECK_LAUNCH("stability probe");
-    ib_count_launch("setup");
-    ib_count_launch("setup");
     return IB_OK;
 }
 
@@ -2108,6 +2118,7 @@ static ib_status build_stag_plan(ib_table* t, const std::vector<PlanOp>& ops, in
     cons.rpb = d_rb;
     cons.rpe = d_re;
     cons.in = partial;
+    cons.n_in = npid;
     return IB_OK;
 }
 
@@ -2249,7 +2260,8 @@ static ib_status forward_stag(ib_table* t, const ib_shot* sh, double dt, int nt,
             ProfToken tk = ib_prof_begin(kname<T>("stag_graph50_f32", "stag_graph50_f64"), cs);
             IB_CUDA(cudaGraphLaunch(exec, cs));
             ib_prof_end(tk, cs);
-            if (probe) TRY(probe_rescale<T>(probe, r + 1, L.total, p, vx, vz, cs));
+            if (probe)
+                TRY(probe_rescale<T>(probe, r + 1, L.total, p, vx, vz, cs, const_cast<T*>(a.pv.in), a.pv.n_in));
             for (int k = 0; k < K; ++k) {
                 ib_count_launch(kname<T>("stag_v2d_f32", "stag_v2d_f64"));
                 ib_count_launch(kname<T>("stag_p2d_f32", "stag_p2d_f64"));
@@ -2264,7 +2276,8 @@ static ib_status forward_stag(ib_table* t, const ib_shot* sh, double dt, int nt,
         a.rec_step = k - 1;
         TRY(launch_step(cs, true));
         if (probe && (nrep * K + k + 1) % STAB_BLOCK == 0)
-            TRY(probe_rescale<T>(probe, (nrep * K + k + 1) / STAB_BLOCK, L.total, p, vx, vz, cs));
+            TRY(probe_rescale<T>(probe, (nrep * K + k + 1) / STAB_BLOCK, L.total, p, vx, vz, cs,
+                                 const_cast<T*>(a.pv.in), a.pv.n_in));
     }
     if (g.rec.n) {
         k_receivers<T><<<grid1(g.rec.n, 256), 256, 0, cs>>>(g.rec, p, (T*)sh->traces_dev, nt, nt - 1);
