@@ -214,6 +214,12 @@ __device__ __forceinline__ T damp_a(const Layout& L, int dw, T da, int64_t x, in
     const T r = (T)d2 / (T)(w * w);
     return da * (r < (T)1 ? r : (T)1);
 }
+// does the box [x0, x1] x [y0, y1] x [.., z1] reach into the layer (dw > 0)?
+__device__ __forceinline__ bool damp_box(const Layout& L, int dw, int64_t x0, int64_t x1, int64_t y0, int64_t y1,
+                                         int64_t z1) {
+    return dw > 0 && (x0 < dw || x1 > L.nx - 1 - dw || z1 > L.nz - 1 - dw ||
+                      (L.ndim == 3 && (y0 < dw || y1 > L.ny - 1 - dw)));
+}
 template <typename T>
 __device__ __forceinline__ T damp_g(const Layout& L, int dw, T da, int64_t x, int64_t y, int64_t z) {
     const T av = damp_a<T>(L, dw, da, x, y, z);
@@ -284,6 +290,7 @@ __device__ __forceinline__ void leap2d_tile(const StepArgs<T>& a, int64_t bx, in
     __syncthreads();
     if (e1 > e0) add_entries_range(a.op, e0, e1, a.p, origin, acc, tid, 256);
     __syncthreads();
+    const bool damped = damp_box(L, a.dw, x0, x0 + TX - 1, 0, 0, z0 + TZ - 1);
 #pragma unroll
     for (int j = 0; j < PT; ++j) {
         const int i = tid + 256 * j, lz = i / TX, lx = i - lz * TX;
@@ -291,7 +298,7 @@ __device__ __forceinline__ void leap2d_tile(const StepArgs<T>& a, int64_t bx, in
         const int64_t q = origin + lz * L.px + lx;
         const T c = tile[lz + H][lx + H];
         T u = c + ((c - pmv[j]) + khv[j] * acc[i]) + sadd[i];
-        if (a.dw) u -= damp_g<T>(L, a.dw, a.da, x0 + lx, 0, z0 + lz) * (u - pmv[j]);
+        if (damped) u -= damp_g<T>(L, a.dw, a.da, x0 + lx, 0, z0 + lz) * (u - pmv[j]);
         a.out[q] = u;
     }
 }
@@ -490,13 +497,14 @@ __device__ __forceinline__ void leap2d_strip(const StepArgs<float>& a, int64_t b
         }
         const float* pmS = sm.pm[st];
         const float* khS = sm.kh[st];
+        const bool damped = damp_box(L, a.dw, x0, x0 + TX - 1, 0, 0, zs + (s + 1) * TZ - 1);
 #pragma unroll
         for (int j = 0; j < 2; ++j) {
             const int i = i0 + j * TX;
             if (xin && s * TZ + j < zleft) {
                 const float c = cv[j];
                 float u = c + ((c - pmS[i]) + khS[i] * sm.acc[i]) + sm.sadd[i];
-                if (a.dw) u -= damp_g<float>(L, a.dw, a.da, x0 + lx, 0, zs + s * TZ + lz0 + j) * (u - pmS[i]);
+                if (damped) u -= damp_g<float>(L, a.dw, a.da, x0 + lx, 0, zs + s * TZ + lz0 + j) * (u - pmS[i]);
                 outp[j * L.px] = u;
             }
             sm.sadd[i] = 0.f;
@@ -660,7 +668,7 @@ __global__ void __launch_bounds__(256) k_leap3d(StepArgs<T> a, int zchunk, int64
             T c = q[H];
             const T pmq = a.pm[qi];
             T u = c + ((c - pmq) + a.Kh[qi] * acc[tid]) + sadd[tid];
-            if (a.dw) u -= damp_g<T>(L, a.dw, a.da, x, y, z) * (u - pmq);
+            if (a.dw && damp_box(L, a.dw, x, x, y, y, z)) u -= damp_g<T>(L, a.dw, a.da, x, y, z) * (u - pmq);
             a.out[qi] = u;
         }
 #pragma unroll
@@ -768,6 +776,7 @@ __global__ void __launch_bounds__(256) k_leap3d_tma(StepArgs<float> a, const __g
     const int64_t zlast = ze - 1 + H;                 // last plane fetched by TMA
     const bool col_ok = x < L.nx + H && y < L.ny + H;
     const bool valid = x < L.nx && y < L.ny;
+    const bool damped_xy = damp_box(L, a.dw, x0, x0 + TX - 1, y0, y0 + TY - 1, 0);
     // tensor row of plane z, tile row y0 - H: (H + 1 + z) * py + y0
     auto plane_row = [&](int64_t z) { return (int)((H + 1 + z) * L.py + y0); };
     if (tid == 0) {
@@ -865,7 +874,7 @@ __global__ void __launch_bounds__(256) k_leap3d_tma(StepArgs<float> a, const __g
         if (valid) {
             const float c = q[H];
             float u = c + ((c - pm_c) + kh_c * acc[tid]) + sadd[tid];
-            if (a.dw) u -= damp_g<float>(L, a.dw, a.da, x, y, z) * (u - pm_c);
+            if (damped_xy || (a.dw && z > L.nz - 1 - a.dw)) u -= damp_g<float>(L, a.dw, a.da, x, y, z) * (u - pm_c);
             a.out[qc] = u;
         }
 #pragma unroll
@@ -1333,6 +1342,7 @@ __device__ __forceinline__ void adj2d_tile(const AdjArgs<T>& a, int64_t bx, int6
     }
     __syncthreads();
     const T wv = a.src.n ? a.wavelet[a.m - 1] : (T)0;
+    const bool damped = damp_box(L, a.dw, x0, x0 + TX - 1, 0, 0, z0 + TZ - 1);
 #pragma unroll
     for (int j = 0; j < PT; ++j) {
         const int i = tid + 256 * j, lz = i / TX, lx = i - lz * TX;
@@ -1341,15 +1351,15 @@ __device__ __forceinline__ void adj2d_tile(const AdjArgs<T>& a, int64_t bx, int6
         // With an absorbing layer the buffers hold nu = mu / (1 + a): the transpose of
         // p^{n+1} = ((2 + K L) p^n - (1 - a) p^{n-1} + s) / (1 + a) is
         // mu^m = 2 nu^{m+1} - (1 - a) nu^{m+2} + L^T (K nu^{m+1}) + R^T res^{m-1}.
-        const T av = a.dw ? damp_a<T>(L, a.dw, a.da, x0 + lx, 0, z0 + lz) : (T)0;
+        const T av = damped ? damp_a<T>(L, a.dw, a.da, x0 + lx, 0, z0 + lz) : (T)0;
         T mu_new = (T)2 * mu_v[j] - ((T)1 - av) * mum_v[j] + acc[i];
-        if (a.dw) mu_new = mu_new / ((T)1 + av);
+        if (damped) mu_new = mu_new / ((T)1 + av);
         a.out[q] = mu_new;
         const T Kq = kh_v[j];
         if (Kq > (T)0) {
             // dt^2 c^2 (L p^{m-1}) = (1 + a) p^m - 2 p^{m-1} + (1 - a) p^{m-2} - s^{m-1}
             T d2 = (p0_v[j] - p1_v[j]) - (p1_v[j] - p2_v[j]);
-            if (a.dw) d2 += av * (p0_v[j] - p2_v[j]);
+            if (damped) d2 += av * (p0_v[j] - p2_v[j]);
             const T srcw = sw[i];
             d2 -= srcw * wv;
             a.grad[q] = g_v[j] + mu_new * (a.two_dt_over_h / sqrt(Kq)) * d2;
