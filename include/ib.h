@@ -85,12 +85,13 @@ typedef struct {
                               (the paper's value) and 0.25 for the rigid surface
                               (the paper gives none; 0.5 leaves a growing mode)     */
     double eta_v;          /* velocity cut-off eta (paper: 0)                      */
-    double rank_tol;       /* full rank iff sigma_min > rank_tol * sigma_max       */
+    double rank_tol;       /* full rank iff sigma_min > rank_tol * sigma_max; <= 0
+                              -> 1e-3 for the free surface, 1e-2 for the rigid one  */
 } ib_opts;
 
 /* Fill `opts` with the defaults for space order M (basis 0 = min(M, 4), min
- * order 2, radius (basis+1)/2, growth 3, eta_p -1 (by boundary condition),
- * eta_v 0, rank_tol 1e-3). */
+ * order 2, radius (basis+1)/2, growth 3, eta_p -1 and rank_tol -1 (by
+ * boundary condition), eta_v 0). */
 void ib_opts_default(ib_opts* opts, int32_t space_order);
 
 typedef struct ib_table ib_table;   /* opaque, library-owned */

@@ -37,20 +37,21 @@ Readings of the paper used here (the paper is silent or ambiguous):
 * boundary points are in the support if |x_b - x0|^2 <= r^2 + 1e-9;
 * r grows by 0.5 up to r0 + 3; then the basis order drops by 2 (down to 2);
 * rank test: sigma_min > rank_tol * sigma_max of A (SVD), and A has at least
-  as many rows as columns; rank_tol = 1e-3 by default: fits with cond(A) above
-  1e3 count as rank deficient and grow the support.  Accepting ill-conditioned
-  fits (1e-4 .. 1e-10) gives extrapolation weights up to ~1e3 and the 3D
-  order-8 scheme on seeded Gaussian hills then grows exponentially within 500
-  steps; at 1e-3 it stays bounded over 1500 steps (2D unchanged);
+  as many rows as columns.  The paper asks for rank(A) equal to the number of
+  basis terms and gives no tolerance; the default is set per boundary
+  condition from the measured growth per step of the schemes
+  (``oracle.stability``): 1e-3 for the free surface (order-8 basis on the
+  seeded sinusoid: 1.05 at 1e-10, 1.0013 at 1e-3; 512 x 512 x 384 Gaussian
+  hills: 1.0002 at 1e-3, 1.041 at 1e-2) and 1e-2 for the rigid surface
+  (hills: 1.076 at 1e-3, 1.00002 at 1e-2; sinusoid with eta 0.25: 1.00064 at
+  1e-3, 1.00011 at 1e-2);
 * expansion point: the stencil centre (2nd-order form); the node receiving the
   derivative (staggered form);
 * eta of the pressure fits: 0.5 for the free surface, as the paper sets it
   (2D example-geometry paragraph), and 0.25 for the rigid surface, for which
-  the paper gives no value.  With 0.5 the rigid second-order scheme has a
-  growing mode on the seeded Gaussian hills (growth per step 1.10 on a
-  34 x 34 x 30 crop, 1.076 on the 512 x 512 x 384 model) and on the seeded
-  sinusoid (1.0021); with 0.25 the growth is 1.0004 and 1.00015.  Larger eta
-  makes it worse (0.75: 1.17, 1.0: 1.52 on the crop);
+  the paper gives no value (rigid, rank tolerance 1e-2, seeded sinusoid:
+  growth per step 1.0026 at eta 0.5, 1.00011 at 0.25; at rank tolerance 1e-3
+  on a 34 x 34 x 30 hills crop: 1.10 at 0.5, 1.0004 at 0.25, 1.17 at 0.75);
 * basis order of the extrapolants (``Opts.basis``): min(M, 4) by default.
   The paper asks for a basis of the interior order for consistent error (3D
   expansion paragraph of "Constructing Finite-Difference Approximations") and
@@ -79,7 +80,7 @@ class RankError(RuntimeError):
 
 class Opts:
     def __init__(self, M, eta_p=None, eta_v=0.0, radius=0.0, growth=3.0,
-                 min_order=2, rank_tol=1e-3, ib_order=0):
+                 min_order=2, rank_tol=None, ib_order=0):
         self.M = int(M)
         # basis order of the extrapolants (<= M); 0 selects min(M, 4) (see basis)
         self.ib_order = int(ib_order)
@@ -89,7 +90,17 @@ class Opts:
         self.radius = float(radius)
         self.growth = float(growth)
         self.min_order = int(min_order)
-        self.rank_tol = float(rank_tol)
+        # rank tolerance; None selects the default of for_bc
+        self.rank_tol = None if rank_tol is None else float(rank_tol)
+
+    def for_bc(self, bc):
+        """These options with the boundary-condition defaults filled in: rank
+        tolerance 1e-3 (free) or 1e-2 (rigid); eta_p as eta_pressure(bc)."""
+        out = Opts(self.M, eta_p=self.eta_pressure(bc), eta_v=self.eta_v, radius=self.radius,
+                   growth=self.growth, min_order=self.min_order,
+                   rank_tol=self.rank_tol if self.rank_tol is not None else (1e-3 if bc == "free" else 1e-2),
+                   ib_order=self.ib_order)
+        return out
 
     def eta_pressure(self, bc):
         """eta of the pressure fits: eta_p if set, else 0.5 for the free surface
@@ -285,6 +296,7 @@ def laplacian_rows(geom, bc, opts, nodes=None):
 
     Returns dict node -> (dict offset -> weight, info).
     """
+    opts = opts.for_bc(bc)
     M = opts.M
     w2 = [float(x) for x in taylor.central_second(M)]
     H = M // 2
@@ -346,6 +358,7 @@ def gradient_rows(geom, a, bc, opts, nodes=None):
     field with the pressure BC hierarchy and eta_p.
     Returns dict node j -> (dict p-offset -> weight, info).
     """
+    opts = opts.for_bc(bc)
     M = opts.M
     c = [float(x) for x in taylor.staggered_first(M)]      # at offsets -(M-1)/2..(M-1)/2
     fields = [Field(geom.mask, np.zeros(geom.d), opts.eta_pressure(bc))]
@@ -381,6 +394,7 @@ def divergence_rows(geom, bc, opts, nodes=None):
     the velocity BC hierarchy and eta_v.
     Returns dict node -> (dict (component, v-offset) -> weight, info).
     """
+    opts = opts.for_bc(bc)
     M = opts.M
     d = geom.d
     c = [float(x) for x in taylor.staggered_first(M)]

@@ -83,17 +83,19 @@ def test_stability_default_matches_oracle_power_iteration():
 def test_stability_staggered_matches_oracle():
     """Staggered form, rigid surface on the seeded sinusoid (default options):
     the growth per step of the library's power iteration (FP64) and the
-    oracle's agree (both about 1.001: the rigid velocity fits leave a weakly
+    oracle's agree (about 1.0018: the rigid velocity fits leave a weakly
     growing mode)."""
     ws = inputs.workload_sinusoid_staggered(nx=61, nz=75, h=5.0, M=8, nt=10, bc="rigid")
     s = sim.Staggered(ws["sdf"], ws["vel"], ws["rho"], 5.0, 8, "rigid", ws["dt"], ws["src"], ws["rec"][:4])
-    r_orc, _ = stability.staggered_growth(s.G, s.D, s.bv, s.kp, nsteps=3000)
+    # 8000 steps: power iterations from different random starts agree to
+    # ~2e-5 there (at 3000 steps they still spread over 1.0006 .. 1.0016)
+    r_orc, _ = stability.staggered_growth(s.G, s.D, s.bv, s.kp, nsteps=8000)
     assert r_orc > 1.0005
     t = ib.ib_build_stencils(cuda(ws["sdf"]), 5.0, "rigid", "staggered", 8)
-    g, st = ib.ib_stability(t, cuda(ws["vel"].astype(np.float64)), ws["dt"], 3000,
+    g, st = ib.ib_stability(t, cuda(ws["vel"].astype(np.float64)), ws["dt"], 8000,
                             rho=cuda(ws["rho"].astype(np.float64)), max_gain=1e30)
     record("staggered_rigid_growth", gpu=g, oracle=r_orc)
-    assert abs(g - r_orc) <= 0.2 * (r_orc - 1.0) + 2e-5, (g, r_orc)
+    assert abs(g - r_orc) <= 0.1 * (r_orc - 1.0), (g, r_orc)
 
 
 def test_nonfinite_run_reports_unstable():
