@@ -1965,7 +1965,7 @@ static ib_status run_fit(ib_table* t, const Geo& g, const FitKind& fk, const int
 
 static void free_op(IbOp& op) {
     void* ps[] = {op.row_lin, op.row_pad, op.row_ptr, op.col_code, op.col_pad, op.w64, op.w32, op.row_info,
-                  op.t_row_pad, op.t_ptr, op.t_src_off, op.t_w64, op.t_w32};
+                  op.t_row_pad, op.t_ptr, op.t_src_off, op.t_w64, op.t_w32, op.code16};
     for (void* p : ps)
         if (p) cudaFree(p);
     for (auto& b : op.bins) ib_free_bins(b);
@@ -2340,16 +2340,35 @@ __global__ void k_fill_entries(int64_t n, const int32_t* perm, const int32_t* so
 }
 
 void ib_free_bins(TileBins& b) {
-    void* ps[] = {b.tile_ptr, b.perm, b.ent_ptr, b.ent_loc, b.ent_src, b.ent_w32, b.ent_w64};
+    void* ps[] = {b.tile_ptr, b.perm, b.ent_ptr, b.ent_loc, b.ent_src, b.ent_w32, b.ent_w64,
+                  b.ent_code, b.ent_slot};
     for (void* p : ps)
         if (p) cudaFree(p);
     b = TileBins();
 }
 
+// compact entries: 16-bit footprint code (and one-byte slot) per entry
+__global__ void k_fill_compact(int64_t n, const int32_t* perm, const int32_t* ent_loc, const int64_t* ent_off,
+                               const int64_t* row_ptr, const int32_t* col_code, uint16_t* ent_code,
+                               uint8_t* ent_slot) {
+    for (int64_t k = blockIdx.x; k < n; k += gridDim.x) {
+        const int32_t r = perm[k];
+        const int64_t o = ent_off[k];
+        const int64_t j0 = row_ptr[r], j1 = row_ptr[r + 1];
+        for (int64_t j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
+            int dx, dy, dz;
+            unpack_off(col_code[j], dx, dy, dz);
+            ent_code[o + (j - j0)] = pack_code16(dx, dy, dz);
+            if (ent_slot) ent_slot[o + (j - j0)] = (uint8_t)ent_loc[o];
+        }
+    }
+}
+
 // rows (row_pad) binned by tile; with row_ptr/col_pad/w64 also the flattened entries
+// (and, with col_code, their compact form)
 static ib_status make_bins(const Layout& L, int64_t n, const int64_t* pad, const int64_t* row_ptr,
                            const int64_t* col_pad, const double* w64, int tx, int ty, int tz, TileBins& b,
-                           cudaStream_t s) {
+                           cudaStream_t s, const int32_t* col_code = nullptr) {
     int64_t ntx = (L.nx + tx - 1) / tx;
     int64_t nty = (L.ny + ty - 1) / ty;
     int64_t ntz = (L.nz + tz - 1) / tz;
@@ -2411,10 +2430,39 @@ static ib_status make_bins(const Layout& L, int64_t n, const int64_t* pad, const
                                                      b.ent_loc, b.ent_src, b.ent_w32, b.ent_w64);
         IB_CHECK_LAUNCH("k_fill_entries");
         ib_count_launch("setup");
+        if (col_code) {
+            TRY(dalloc(&b.ent_code, std::max<int64_t>(b.nent, 1)));
+            if ((int64_t)tx * ty * tz <= 256) TRY(dalloc(&b.ent_slot, std::max<int64_t>(b.nent, 1)));
+            k_fill_compact<<<grid_for(n, 1), 64, 0, s>>>(n, b.perm, b.ent_loc, off, row_ptr, col_code, b.ent_code,
+                                                         b.ent_slot);
+            IB_CHECK_LAUNCH("k_fill_compact");
+            ib_count_launch("setup");
+        }
     } else {
         IB_CUDA(cudaMemsetAsync(b.ent_ptr, 0, sizeof(int32_t) * (b.ntiles + 1), s));
     }
     IB_CUDA(cudaStreamSynchronize(s));
+    return IB_OK;
+}
+
+__global__ void k_code16(int64_t nnz, const int32_t* col_code, uint16_t* out) {
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < nnz; j += (int64_t)gridDim.x * blockDim.x) {
+        int dx, dy, dz;
+        unpack_off(col_code[j], dx, dy, dz);
+        out[j] = pack_code16(dx, dy, dz);
+    }
+}
+
+// 16-bit footprint codes of an operator's entries in row order (kept with the table)
+ib_status ib_table_code16(ib_table* t, int op, const uint16_t** out, cudaStream_t s) {
+    IbOp& o = t->ops[op];
+    if (!o.code16 && o.nnz > 0) {
+        TRY(dalloc(&o.code16, o.nnz));
+        k_code16<<<grid_for(o.nnz, 256), 256, 0, s>>>(o.nnz, o.col_code, o.code16);
+        IB_CHECK_LAUNCH("k_code16");
+        ib_count_launch("setup");
+    }
+    *out = o.code16;
     return IB_OK;
 }
 
@@ -2437,7 +2485,7 @@ ib_status ib_table_bins(ib_table* t, int op, bool transposed, int tx, int ty, in
         TRY(ib_table_transpose(t, op, s));
         TRY(make_bins(t->L, o.t_nrows, o.t_row_pad, o.t_ptr, o.t_src_off, o.t_w64, tx, ty, tz, b, s));
     } else {
-        TRY(make_bins(t->L, o.nrows, o.row_pad, o.row_ptr, o.col_pad, o.w64, tx, ty, tz, b, s));
+        TRY(make_bins(t->L, o.nrows, o.row_pad, o.row_ptr, o.col_pad, o.w64, tx, ty, tz, b, s, o.col_code));
     }
     v.push_back(b);
     *out = &v.back();

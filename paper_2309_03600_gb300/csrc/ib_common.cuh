@@ -88,7 +88,17 @@ struct TileBins {             // rows of one operator binned by step tile
     int32_t* ent_src = nullptr;    // source offset from the tile origin (padded index)
     float* ent_w32 = nullptr;
     double* ent_w64 = nullptr;
+    // the same entries in compact form (3D step): a 16-bit footprint code
+    // (dx + 16) | (dy + 16) << 5 | (dz + 16) << 10 and, for tiles of at most 256
+    // nodes, the output slot as one byte: an entry moves 7 bytes (code, slot,
+    // FP32 weight) instead of 12
+    uint16_t* ent_code = nullptr;  // [nent]
+    uint8_t* ent_slot = nullptr;   // [nent]
 };
+
+__host__ __device__ inline uint16_t pack_code16(int dx, int dy, int dz) {
+    return (uint16_t)((dx + 16) | ((dy + 16) << 5) | ((dz + 16) << 10));
+}
 
 // padded index of the first node of a tile (2D: (bx, bz); 3D: (bx, by, z))
 __host__ __device__ inline int64_t tile_origin(const Layout& L, const TileBins& b, int64_t tile) {
@@ -114,6 +124,7 @@ struct IbOp {
     double* w64 = nullptr;
     float* w32 = nullptr;
     int32_t* row_info = nullptr;  // [nrows][4]
+    uint16_t* code16 = nullptr;   // [nnz] pack_code16 footprint codes (built on first use)
     std::vector<TileBins> bins;
     // transposed operator (adjoint): rows keyed by column node
     bool have_t = false;
@@ -159,6 +170,7 @@ ib_status ib_compact(const uint8_t* flags, int64_t n, int64_t** out, int64_t* co
 ib_status ib_table_bins(ib_table* t, int op, bool transposed, int tx, int ty, int tz,
                         const TileBins** out, cudaStream_t s);
 ib_status ib_table_transpose(ib_table* t, int op, cudaStream_t s);
+ib_status ib_table_code16(ib_table* t, int op, const uint16_t** out, cudaStream_t s);
 
 double ib_wall_seconds();
 

@@ -228,6 +228,16 @@ __device__ __forceinline__ T damp_g(const Layout& L, int dw, T da, int64_t x, in
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+// rounded arithmetic that the compiler may not contract into FMAs
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float sub_rn(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double sub_rn(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float fma_(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fma_(double a, double b, double c) { return fma(a, b, c); }
+
 // asynchronous global -> shared copy of B bytes (zero fill when !valid)
 template <int B>
 __device__ __forceinline__ void cp_async(void* dst, const void* src, bool valid) {
@@ -649,13 +659,17 @@ __global__ void __launch_bounds__(256) k_leap3d(StepArgs<T> a, int zchunk, int64
         sadd[tid] = (T)0;
         __syncthreads();
         {
+            // the grouping of the TMA kernel (see there): exact zero on constants
             const T c = q[H];
+            const T c6 = mul_rn((T)6, c);
             T s = 0;
 #pragma unroll
-            for (int k = 1; k <= H; ++k)
-                s += a.w2[k] * (((tile[ty + H][tx + H + k] - c) + (tile[ty + H][tx + H - k] - c)) +
-                                ((tile[ty + H + k][tx + H] - c) + (tile[ty + H - k][tx + H] - c)) +
-                                ((q[H + k] - c) + (q[H - k] - c)));
+            for (int k = 1; k <= H; ++k) {
+                const T g = add_rn(add_rn(add_rn(tile[ty + H][tx + H + k], tile[ty + H][tx + H - k]),
+                                          add_rn(tile[ty + H + k][tx + H], tile[ty + H - k][tx + H])),
+                                   add_rn(q[H + k], q[H - k]));
+                s = fma_(a.w2[k], sub_rn(g, c6), s);
+            }
             acc[tid] = s;
         }
         const int64_t origin = L.idx(x0, y0, z);
@@ -745,25 +759,105 @@ __global__ void k_wait_selftest(int* err) {
     if (!mbar_wait_bounded(&bar, 0)) atomicExch(err, 1);
 }
 
-template <int H>
+// compact corrections of the 3D tile planes (TileBins compact form): entries of
+// tile plane t are [ptr[t], ptr[t + 1]), each an output slot (one byte), a 16-bit
+// footprint code and an FP32 weight
+struct Rows3 {
+    const int32_t* ptr;
+    const uint8_t* slot;
+    const uint16_t* code;
+    const float* w;
+};
+
+// Entries [e0, e1) of a tile plane: each warp takes chunks of 32 consecutive
+// entries, four chunks at a time (four independent gathers in flight per
+// thread); entries of one row are contiguous, so a segmented warp sum leaves one
+// shared-memory atomic per row segment.  Values are read from p^n (L2).
+__device__ __forceinline__ void add_entries3(const Rows3& r, int32_t e0, int32_t e1, const float* prow0,
+                                             int64_t px, int64_t plane, float* acc, int tid) {
+    constexpr int U = 4;
+    const int lane = tid & 31;
+    const int32_t warp_base = (tid & ~31) * U;
+    for (int32_t base = e0 + warp_base; base < e1; base += 256 * U) {
+        int32_t loc[U];
+        float val[U];
+        bool ok[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int32_t e = base + u * 32 + lane;
+            ok[u] = e < e1;
+            float v = 0.f;
+            loc[u] = -1 - lane;
+            if (ok[u]) {
+                const int sl = r.slot[e];
+                const int c = r.code[e];
+                const int dx = (c & 31) - 16, dy = ((c >> 5) & 31) - 16, dz = (c >> 10) - 16;
+                loc[u] = sl;
+                v = r.w[e] * prow0[(int64_t)dz * plane + ((sl >> 5) + dy) * px + (sl & 31) + dx];
+            }
+            val[u] = v;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) seg_add(acc, loc[u], val[u], ok[u], lane);
+    }
+}
+
+template <int H, int D>
 struct Tma3D {
     static constexpr int TX = 32, TY = 8;
     static constexpr int BW = TX + 8;         // x halo 4 on each side (16-byte aligned box)
     static constexpr int BH = TY + 2 * H;
-    static constexpr int NS = H + 6;          // ring slots: planes z .. z + H + 5 (5 planes in flight)
-    static constexpr uint32_t BYTES = BW * BH * 4;
-    static constexpr int SLOT = (BW * BH + 31) / 32 * 32;   // slot stride in floats (128-byte multiple)
+    static constexpr int NS = H + 1 + D;      // ring slots: planes z .. z + H + D (D planes in flight)
+    static constexpr int PF = BW * BH;        // p plane with halo (floats)
+    static constexpr int TF = TX * TY;        // p_prev or K tile (floats)
+    static constexpr int SLOT = (PF + 2 * TF + 31) / 32 * 32;   // slot stride in floats (128-byte multiple)
+    static constexpr uint32_t BYTES = (PF + 2 * TF) * 4;
 };
 
-template <int H>
-__global__ void __launch_bounds__(256) k_leap3d_tma(StepArgs<float> a, const __grid_constant__ CUtensorMap tm,
-                                                    int zchunk, int64_t nty, int* err) {
-    using C = Tma3D<H>;
-    constexpr int TX = C::TX, TY = C::TY, BW = C::BW, NS = C::NS, SLOT = C::SLOT;
-    __shared__ alignas(128) float ring[NS * SLOT];
-    __shared__ alignas(8) uint64_t bar[NS];
-    __shared__ float acc[TY * TX];
-    __shared__ float sadd[TY * TX];
+// Laplacian (difference form) at the centre r0 of a staged plane, z neighbours from
+// the register queue q (centre q[H + O]): sum_k w_k (((a + b) + (d + e)) + (f + g)
+// - 6 c) over the six neighbours at distance k.  For a constant field each group
+// is exactly zero in floating point (6 c rounds like the sum of the pairs), so the
+// discrete operator annihilates constants.
+template <int H, int O>
+__device__ __forceinline__ float lap3_tma(const float* r0, const float (&q)[2 * H + 2], const float* w2) {
+    constexpr int BW = 40;
+    const float c = q[H + O];
+    const float c6 = __fmul_rn(6.f, c);
+    float sum = 0.f;
+#pragma unroll
+    for (int k = 1; k <= H; ++k) {
+        const float g = __fadd_rn(__fadd_rn(__fadd_rn(r0[k], r0[-k]), __fadd_rn(r0[k * BW], r0[-k * BW])),
+                                  __fadd_rn(q[H + O + k], q[H + O - k]));
+        sum = fmaf(w2[k], __fsub_rn(g, c6), sum);
+    }
+    return sum;
+}
+
+// Each block marches a 32 x 8 column tile through its z chunk, two planes per
+// iteration.  Ring slot k holds plane z (with an x halo of 4 and a y halo of H) of
+// p^n, and the tiles of p^{n-1} and of K = dt^2 c^2 / h^2 at plane z: three
+// cp.async.bulk.tensor copies on one mbarrier, issued when the slot's previous
+// plane is done.  The z neighbours come from a register queue fed by the centres of
+// planes z + H and z + H + 1.  The corrections of each tile plane are gathered by
+// all threads (add_entries3): per entry a one-byte output slot, a 16-bit footprint
+// code and an FP32 weight (7 bytes), the value read from p^n in global memory
+// (L2).  Every wait is bounded: on timeout the block records an error, waits
+// (bounded) for the planes already requested, and leaves.
+template <int H, int D>
+__global__ void __launch_bounds__(256, D <= 2 ? 6 : 5) k_leap3d_tma(StepArgs<float> a, const __grid_constant__ CUtensorMap tm,
+                                                    const __grid_constant__ CUtensorMap tmm,
+                                                    const __grid_constant__ CUtensorMap tmk, Rows3 rw, int zchunk,
+                                                    int64_t nty, int* err) {
+    using C = Tma3D<H, D>;
+    constexpr int TX = C::TX, TY = C::TY, BW = C::BW, NS = C::NS, SLOT = C::SLOT, PF = C::PF, TF = C::TF;
+    static_assert(NS >= H + 2, "planes z .. z + H + 1 are resident together");
+    static_assert(BW == 40, "lap3_tma reads rows of 40 floats");
+    extern __shared__ __align__(128) float dsm[];
+    float* ring = dsm;                                  // NS * SLOT
+    float* acc = ring + NS * SLOT;                      // [2][TY * TX]
+    float* sadd = acc + 2 * TY * TX;                    // [2][TY * TX]
+    uint64_t* bar = (uint64_t*)(sadd + 2 * TY * TX);    // NS
     const int tx = threadIdx.x, ty = threadIdx.y;
     const int tid = ty * TX + tx;
     const int64_t blk = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
@@ -773,56 +867,75 @@ __global__ void __launch_bounds__(256) k_leap3d_tma(StepArgs<float> a, const __g
     const int64_t x = x0 + tx, y = y0 + ty;
     const int64_t zb = (int64_t)blockIdx.z * zchunk;
     const int64_t ze = min(zb + zchunk, L.nz);
-    const int64_t zlast = ze - 1 + H;                 // last plane fetched by TMA
+    const int64_t zlast = ze - 1 + H;                 // last p plane fetched
     const bool col_ok = x < L.nx + H && y < L.ny + H;
     const bool valid = x < L.nx && y < L.ny;
     const bool damped_xy = damp_box(L, a.dw, x0, x0 + TX - 1, y0, y0 + TY - 1, 0);
-    // tensor row of plane z, tile row y0 - H: (H + 1 + z) * py + y0
-    auto plane_row = [&](int64_t z) { return (int)((H + 1 + z) * L.py + y0); };
+    // tensor rows: p plane z, tile row y0 - H at (H + 1 + z) py + y0; tile row y0 at + H
+    auto prow = [&](int64_t z) { return (int)((H + 1 + z) * L.py + y0); };
+    // slot for plane zz: p box always; the p_prev / K tiles only for planes the block updates
+    auto issue = [&](int slot, int64_t zz) {
+        const bool upd = zz < ze;
+        mbar_expect_tx(&bar[slot], (uint32_t)(PF * 4 + (upd ? 2 * TF * 4 : 0)));
+        float* dst = ring + slot * SLOT;
+        tma_load_2d(dst, &tm, (int)(x0 - 4), prow(zz), &bar[slot]);
+        if (upd) {
+            tma_load_2d(dst + PF, &tmm, (int)x0, prow(zz) + H, &bar[slot]);
+            tma_load_2d(dst + PF + TF, &tmk, (int)x0, prow(zz) + H, &bar[slot]);
+        }
+    };
+    // bounded wait for plane zz of this chunk
+    auto wait_plane = [&](int64_t zz) {
+        const int ip = (int)(zz - zb);
+        return mbar_wait_bounded(&bar[ip % NS], (uint32_t)((ip / NS) & 1));
+    };
     if (tid == 0) {
         for (int i = 0; i < NS; ++i) mbar_init(&bar[i], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    if (tid == 0) {
-        for (int i = 0; i < NS && zb + i <= zlast; ++i) {
-            mbar_expect_tx(&bar[i], C::BYTES);
-            tma_load_2d(&ring[i * SLOT], &tm, (int)(x0 - 4), plane_row(zb + i), &bar[i]);
-        }
-    }
-    float q[2 * H + 1];
+    if (tid == 0)
+        for (int i = 0; i < NS && zb + i <= zlast; ++i) issue(i, zb + i);
+    float q[2 * H + 2];
 #pragma unroll
     for (int k = 0; k < 2 * H; ++k) q[k] = col_ok ? a.p[L.idx(x, y, zb - H + k)] : 0.f;
     const float wv = a.src.n ? a.wavelet[a.step] : 0.f;
-    // p_prev and Kh are read two planes ahead of use
-    int64_t qi = L.idx(x, y, zb);
-    float pm_a = valid ? a.pm[qi] : 0.f, kh_a = valid ? a.Kh[qi] : 0.f;
-    float pm_b = 0.f, kh_b = 0.f;
-    if (valid && zb + 1 < ze) {
-        pm_b = a.pm[qi + L.plane];
-        kh_b = a.Kh[qi + L.plane];
-    }
-    // read ahead: the correction range of the next tile plane, and this thread's source corner
-    const int64_t tile_z = nty * a.op.ntx;                  // tiles per plane
+    const int64_t tile_z = nty * a.op.ntx;              // tiles per plane
     const int64_t tile0 = (int64_t)blockIdx.y * a.op.ntx + blockIdx.x;
-    int32_t e0n = 0, e1n = 0;
-    if (a.op.ptr) {
-        e0n = a.op.ptr[zb * tile_z + tile0];
-        e1n = a.op.ptr[zb * tile_z + tile0 + 1];
-    }
     const bool src_me = tid < 8 * a.src.n;
     const int64_t s_idx = src_me ? a.src.idx[tid] : 0;
     const float s_w = src_me ? a.src.w[tid] : 0.f;
-    for (int64_t z = zb; z < ze; ++z) {
-        const int it = (int)(z - zb);
-        const int st = it % NS, sf = (it + H) % NS;
-        const int32_t e0 = e0n, e1 = e1n;
-        if (a.op.ptr && z + 1 < ze) {
-            e0n = a.op.ptr[(z + 1) * tile_z + tile0];
-            e1n = a.op.ptr[(z + 1) * tile_z + tile0 + 1];
+    int64_t qi = L.idx(x, y, zb);
+    for (int64_t z = zb; z < ze; z += 2) {
+        const bool two = z + 1 < ze;
+        const int ia = (int)(z - zb);
+        // entry ranges of the two tile planes (read while the planes are waited for)
+        int32_t ea0 = 0, ea1 = 0, eb0 = 0, eb1 = 0;
+        if (rw.ptr) {
+            const int32_t* pp = rw.ptr + z * tile_z + tile0;
+            ea0 = pp[0];
+            ea1 = pp[1];
+            if (two) {
+                eb0 = pp[tile_z];
+                eb1 = pp[tile_z + 1];
+            }
         }
-        bool ok = mbar_wait_bounded(&bar[st], (uint32_t)((it / NS) & 1));
-        ok = ok && mbar_wait_bounded(&bar[sf], (uint32_t)(((it + H) / NS) & 1));
+        bool ok = wait_plane(z) && wait_plane(z + H);
+        if (two) ok = ok && wait_plane(z + 1) && wait_plane(z + 1 + H);
+        // (after a failed wait the reads below see stale shared memory; the barrier
+        // that follows them tells every thread, and the block leaves)
+        const float* ra = ring + (ia % NS) * SLOT;           // plane z, row j <-> y0 - H + j
+        const float* rb = ring + ((ia + 1) % NS) * SLOT;     // plane z + 1
+        const int ci = (H + ty) * BW + 4 + tx;
+        q[2 * H] = ring[((ia + H) % NS) * SLOT + ci];
+        q[2 * H + 1] = two ? ring[((ia + H + 1) % NS) * SLOT + ci] : 0.f;
+        const float pma = ra[PF + tid], kha = ra[PF + TF + tid];
+        const float pmb = rb[PF + tid], khb = rb[PF + TF + tid];
+        acc[tid] = lap3_tma<H, 0>(ra + ci, q, a.w2);
+        acc[TX * TY + tid] = lap3_tma<H, 1>(rb + ci, q, a.w2);
+        sadd[tid] = 0.f;
+        sadd[TX * TY + tid] = 0.f;
+        const int64_t origin = L.idx(x0, y0, z);
         if (__syncthreads_or(!ok)) {
             if (tid == 0) {
                 atomicExch(err, 1);
@@ -830,69 +943,129 @@ __global__ void __launch_bounds__(256) k_leap3d_tma(StepArgs<float> a, const __g
                 // (planes z .. z + NS - 1), so that no copy is still landing in this
                 // block's shared memory when it leaves
                 const int64_t ziss = min(z + NS - 1, zlast);
-                for (int64_t zp = z; zp <= ziss; ++zp) {
-                    const int ip = (int)(zp - zb);
-                    mbar_wait_bounded(&bar[ip % NS], (uint32_t)((ip / NS) & 1));
-                }
+                for (int64_t zp = z; zp <= ziss; ++zp) wait_plane(zp);
             }
             return;
         }
-        // software pipeline: p_prev and Kh of plane z + 2
-        const float pm_c = pm_a, kh_c = kh_a;
-        const int64_t qc = qi;
-        pm_a = pm_b;
-        kh_a = kh_b;
-        if (valid && z + 2 < ze) {
-            pm_b = a.pm[qi + 2 * L.plane];
-            kh_b = a.Kh[qi + 2 * L.plane];
-        }
-        qi += L.plane;
-        const float* rt = ring + st * SLOT;          // plane z, row j <-> y0 - H + j
-        q[2 * H] = ring[sf * SLOT + (H + ty) * BW + 4 + tx];
-        sadd[tid] = 0.f;
-        {
-            const float c = q[H];
-            float sum = 0.f;
-#pragma unroll
-            for (int k = 1; k <= H; ++k)
-                sum += a.w2[k] * (((rt[(H + ty) * BW + 4 + tx + k] - c) + (rt[(H + ty) * BW + 4 + tx - k] - c)) +
-                                  ((rt[(H + ty + k) * BW + 4 + tx] - c) + (rt[(H + ty - k) * BW + 4 + tx] - c)) +
-                                  ((q[H + k] - c) + (q[H - k] - c)));
-            acc[tid] = sum;
-        }
-        const int64_t origin = L.idx(x0, y0, z);
-        __syncthreads();
         if (src_me && s_w != 0.f) {
             const int64_t rel = s_idx - origin;
             if (rel >= 0) {
-                const int64_t ly = rel / L.px, lx = rel - ly * L.px;
-                if (ly < TY && lx < TX) atomicAdd(&sadd[ly * TX + lx], s_w * wv);
+                const int64_t lz = rel / L.plane, r2 = rel - lz * L.plane;
+                const int64_t ly = r2 / L.px, lx = r2 - ly * L.px;
+                if (lz < (two ? 2 : 1) && ly < TY && lx < TX) atomicAdd(&sadd[lz * TX * TY + ly * TX + lx], s_w * wv);
             }
         }
-        if (e1 > e0) add_entries_range(a.op, e0, e1, a.p, origin, acc, tid, 256);
+        if (ea1 > ea0) add_entries3(rw, ea0, ea1, a.p + origin, L.px, L.plane, acc, tid);
+        if (eb1 > eb0) add_entries3(rw, eb0, eb1, a.p + origin + L.plane, L.px, L.plane, acc + TX * TY, tid);
         __syncthreads();
-        if (valid) {
-            const float c = q[H];
-            float u = c + ((c - pm_c) + kh_c * acc[tid]) + sadd[tid];
-            if (damped_xy || (a.dw && z > L.nz - 1 - a.dw)) u -= damp_g<float>(L, a.dw, a.da, x, y, z) * (u - pm_c);
-            a.out[qc] = u;
-        }
-#pragma unroll
-        for (int k = 0; k < 2 * H; ++k) q[k] = q[k + 1];
-        __syncthreads();
-        // slot st is free: fetch plane z + NS into it
-        if (tid == 0 && z + NS <= zlast) {
+        // the two slots are free (p_prev and K read above, the stencils done): the
+        // planes NS further into them
+        if (tid == 0) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_expect_tx(&bar[st], C::BYTES);
-            tma_load_2d(&ring[st * SLOT], &tm, (int)(x0 - 4), plane_row(z + NS), &bar[st]);
+            if (z + NS <= zlast) issue(ia % NS, z + NS);
+            if (two && z + 1 + NS <= zlast) issue((ia + 1) % NS, z + 1 + NS);
         }
+        if (valid) {
+            float u = q[H] + ((q[H] - pma) + kha * acc[tid]) + sadd[tid];
+            if (damped_xy || (a.dw && z > L.nz - 1 - a.dw)) u -= damp_g<float>(L, a.dw, a.da, x, y, z) * (u - pma);
+            a.out[qi] = u;
+            if (two) {
+                float ub = q[H + 1] + ((q[H + 1] - pmb) + khb * acc[TX * TY + tid]) + sadd[TX * TY + tid];
+                if (damped_xy || (a.dw && z + 1 > L.nz - 1 - a.dw))
+                    ub -= damp_g<float>(L, a.dw, a.da, x, y, z + 1) * (ub - pmb);
+                a.out[qi + L.plane] = ub;
+            }
+        }
+        qi += 2 * L.plane;
+#pragma unroll
+        for (int k = 0; k < 2 * H; ++k) q[k] = q[k + 2];
     }
     // planes fetched past the chunk that no iteration waited for (chunks shorter than H):
     // complete them before the block leaves
     bool ok = true;
-    for (int it = (int)(ze - zb); it <= (int)(zlast - zb); ++it)
-        ok = ok && mbar_wait_bounded(&bar[it % NS], (uint32_t)((it / NS) & 1));
+    for (int64_t zz = ze; zz <= zlast; ++zz) ok = ok && wait_plane(zz);
     if (!ok && tid == 0) atomicExch(err, 1);
+}
+
+// Corrections of the modified Laplacian for a 3D step whose kernel applied the
+// standard stencil only, over all IB rows of the grid at once:
+//   out[q] += (1 - g(q)) K[q] sum_j w_j p[q + off_j]
+// (g the absorbing-layer factor of the step, 0 outside the layer), entries as a
+// 16-bit footprint code and an FP32 weight in row order.  A group of 8 lanes takes
+// one row (a warp four rows), each lane up to four entries per round with their
+// gathers in flight together, and the sum is added with a reduction that returns
+// nothing (rows are distinct nodes), so no lane waits on it.
+__global__ void __launch_bounds__(256) k_ib_add3(int64_t nrows, const int64_t* __restrict__ row_pad,
+                                                 const int64_t* __restrict__ row_ptr,
+                                                 const uint16_t* __restrict__ code, const float* __restrict__ w,
+                                                 const float* __restrict__ p, const float* __restrict__ Kh,
+                                                 float* out, Layout L, int dw, float da) {
+    const int lane = threadIdx.x & 31, gl = lane & 7;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    auto gather = [&](int64_t q, int c) {
+        return p[q + (int64_t)((c >> 10) - 16) * L.plane + (int64_t)(((c >> 5) & 31) - 16) * L.px + ((c & 31) - 16)];
+    };
+    for (int64_t rb = warp * 4; rb < nrows; rb += nwarp * 4) {
+        const int64_t r = rb + (lane >> 3);
+        const bool act = r < nrows;
+        const int64_t q = act ? row_pad[r] : 0;
+        const int64_t j0 = act ? row_ptr[r] : 0, j1 = act ? row_ptr[r + 1] : 0;
+        float v = 0.f;
+        for (int64_t j = j0 + gl; j < j1; j += 32) {
+            float wv[4], pv[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int64_t e = j + 8 * u;
+                const bool ok = e < j1;
+                const int c = ok ? code[e] : 16 | (16 << 5) | (16 << 10);
+                wv[u] = ok ? w[e] : 0.f;
+                pv[u] = gather(q, c);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) v += wv[u] * pv[u];
+        }
+        v += __shfl_xor_sync(0xffffffffu, v, 4, 8);
+        v += __shfl_xor_sync(0xffffffffu, v, 2, 8);
+        v += __shfl_xor_sync(0xffffffffu, v, 1, 8);
+        if (act && gl == 0) {
+            float add = Kh[q] * v;
+            if (dw) {
+                const int64_t rel = q - L.base, z = rel / L.plane, rem = rel - z * L.plane;
+                const int64_t y = rem / L.px, x = rem - y * L.px;
+                add *= 1.f - damp_g<float>(L, dw, da, x, y, z);
+            }
+            atomicAdd(&out[q], add);
+        }
+    }
+}
+
+template <int H, int D>
+static size_t tma3d_smem() {
+    using C = Tma3D<H, D>;
+    return sizeof(float) * ((size_t)C::NS * C::SLOT + 4 * C::TX * C::TY) + sizeof(uint64_t) * C::NS;
+}
+
+// planes in flight per block: 3 by default (IB_RING=2 or 5 selects 2 or 5, for tuning)
+template <int H>
+static void launch_leap3d_tma(const StepArgs<float>& a, const CUtensorMap& tm, const CUtensorMap& tmm,
+                              const CUtensorMap& tmk, const Rows3& rw, int zchunk, int64_t nty, int* err, dim3 grid,
+                              cudaStream_t s) {
+    static const int ring = [] {
+        const char* e = getenv("IB_RING");
+        const int r = e ? atoi(e) : 3;
+        return r == 5 || r == 2 ? r : 3;
+    }();
+    const dim3 blk(32, 8);
+    if (ring == 2) {
+        k_leap3d_tma<H, 2><<<grid, blk, tma3d_smem<H, 2>(), s>>>(a, tm, tmm, tmk, rw, zchunk, nty, err);
+    } else if (ring == 5) {
+        const size_t sm = tma3d_smem<H, 5>();
+        cudaFuncSetAttribute(k_leap3d_tma<H, 5>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_leap3d_tma<H, 5><<<grid, blk, sm, s>>>(a, tm, tmm, tmk, rw, zchunk, nty, err);
+    } else {
+        k_leap3d_tma<H, 3><<<grid, blk, tma3d_smem<H, 3>(), s>>>(a, tm, tmm, tmk, rw, zchunk, nty, err);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1687,10 +1860,11 @@ static bool tma_enabled() {
 }
 
 // 2D view of a padded FP32 3D field: rows of px elements; box (32 + 8) x (8 + 2H)
-static ib_status make_plane_map(CUtensorMap& tm, void* base, const Layout& L) {
+// (a plane with its halo) or, with tile_only, 32 x 8 (a tile without halo)
+static ib_status make_plane_map(CUtensorMap& tm, void* base, const Layout& L, bool tile_only = false) {
     cuuint64_t dims[2] = {(cuuint64_t)L.px, (cuuint64_t)(L.total / L.px)};
     cuuint64_t strides[1] = {(cuuint64_t)L.px * 4};
-    cuuint32_t box[2] = {32 + 8, (cuuint32_t)(8 + 2 * L.H)};
+    cuuint32_t box[2] = {tile_only ? 32u : 32u + 8u, tile_only ? 8u : (cuuint32_t)(8 + 2 * L.H)};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = tma_encode_fn()(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
                                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -1864,17 +2038,38 @@ static ib_status forward_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, 
     const bool strips = d == 2 && sizeof(T) == 4 && use_strips(L);
     dim3 grids((unsigned)((L.nx + TX2 - 1) / TX2),
                (unsigned)(((L.nz + TZ2 - 1) / TZ2 + STRIP_NSUB - 1) / STRIP_NSUB));
-    const int zchunk = 32;
+    // planes per 3D block (IB_ZCHUNK overrides it for tuning)
+    int zchunk = 32;
+    if (const char* e = getenv("IB_ZCHUNK")) zchunk = std::max(1, atoi(e));
     dim3 grid3((unsigned)((L.nx + 31) / 32), (unsigned)((L.ny + 7) / 8), (unsigned)((L.nz + zchunk - 1) / zchunk));
     const int64_t nty3 = (L.ny + 7) / 8;
-    // FP32 3D: TMA-staged plane tiles (one tensor map per wavefield buffer)
-    CUtensorMap tmap[2];
+    // FP32 3D: TMA-staged planes of p (with halo) and tiles of p_prev and K (one
+    // tensor map of each kind per buffer), compact correction rows
+    CUtensorMap tmap[2], tmtile[2], tmK;
+    Rows3 rows3;
+    memset(&rows3, 0, sizeof rows3);
+    const uint16_t* code16 = nullptr;
     int* err = nullptr;
     const bool use_tma = d == 3 && sizeof(T) == 4 && tma_enabled();
     if (use_tma) {
         TRY(make_plane_map(tmap[0], (void*)p0, L));
         TRY(make_plane_map(tmap[1], (void*)p1, L));
+        TRY(make_plane_map(tmtile[0], (void*)p0, L, true));
+        TRY(make_plane_map(tmtile[1], (void*)p1, L, true));
+        TRY(make_plane_map(tmK, (void*)Kh, L, true));
         TRY(S.alloc(&err, 1, true));
+        // corrections: fused into the step kernel (IB_FUSED3=1) or added by k_ib_add3
+        const char* fe = getenv("IB_FUSED3");
+        if (fe && fe[0] == '1') {
+            if (bins && bins->nent > 0) {
+                rows3.ptr = bins->ent_ptr;
+                rows3.slot = bins->ent_slot;
+                rows3.code = bins->ent_code;
+                rows3.w = bins->ent_w32;
+            }
+        } else if (t->ops[0].nrows > 0) {
+            TRY(ib_table_code16(t, 0, &code16, s));
+        }
     }
     for (int n = 0; n < nt; ++n) {
         if (ckpt && n % seg == 0) {
@@ -1894,13 +2089,22 @@ static ib_status forward_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, 
         } else if (use_tma) {
             dim3 blk(32, 8);
             const CUtensorMap& tmc = (cur == p0) ? tmap[0] : tmap[1];
+            const CUtensorMap& tmm = (cur == p0) ? tmtile[1] : tmtile[0];   // p_prev: the other buffer
             PROF_LAUNCH("leap3d_tma_f32", s, {
                 const StepArgs<float>& af = *reinterpret_cast<const StepArgs<float>*>(&a);
-                if (H == 1) k_leap3d_tma<1><<<grid3, blk, 0, s>>>(af, tmc, zchunk, nty3, err);
-                else if (H == 2) k_leap3d_tma<2><<<grid3, blk, 0, s>>>(af, tmc, zchunk, nty3, err);
-                else if (H == 3) k_leap3d_tma<3><<<grid3, blk, 0, s>>>(af, tmc, zchunk, nty3, err);
-                else k_leap3d_tma<4><<<grid3, blk, 0, s>>>(af, tmc, zchunk, nty3, err);
+                if (H == 1) launch_leap3d_tma<1>(af, tmc, tmm, tmK, rows3, zchunk, nty3, err, grid3, s);
+                else if (H == 2) launch_leap3d_tma<2>(af, tmc, tmm, tmK, rows3, zchunk, nty3, err, grid3, s);
+                else if (H == 3) launch_leap3d_tma<3>(af, tmc, tmm, tmK, rows3, zchunk, nty3, err, grid3, s);
+                else launch_leap3d_tma<4>(af, tmc, tmm, tmK, rows3, zchunk, nty3, err, grid3, s);
             });
+            if (code16) {
+                const IbOp& op = t->ops[0];
+                PROF_LAUNCH("ib_add3_f32", s, {
+                    k_ib_add3<<<grid1(op.nrows * 32, 256), 256, 0, s>>>(
+                        op.nrows, op.row_pad, op.row_ptr, code16, op.w32, (const float*)a.p, (const float*)Kh,
+                        (float*)a.out, L, a.dw, (float)a.da);
+                });
+            }
         } else {
             dim3 blk(32, 8);
             PROF_LAUNCH(kname<T>("leap3d_f32", "leap3d_f64"), s, {
