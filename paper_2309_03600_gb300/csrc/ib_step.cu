@@ -2509,6 +2509,209 @@ static ib_status forward_stag(ib_table* t, const ib_shot* sh, double dt, int nt,
     return IB_OK;
 }
 
+// ---------------------------------------------------------------------------
+// 3D staggered pressure-velocity (1st-order section: the paper's signs and the
+// backward-staggered base stencil; 3D first-order example), one thread per node:
+//   v_a[j] (at j + e_a/2) += b_a[j] (sum_k c_k (p[j + k e_a] - p[j - (k-1) e_a]) + G_a corrections)
+//   p[j] += kp[j] (sum_a sum_k c_k (v_a[j + (k-1) e_a] - v_a[j - k e_a]) + D corrections) + src
+// with b_a = dt / (rho h) (mean of 1/rho at the two nodes) and kp = dt rho c^2 / h.
+// The corrections of the modified rows follow each update in a pass over the
+// rows of each operator (k_ib_rows, 8 lanes per row): the updated field is not
+// read by its own update, so the pass sees the same values the fused sum would.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void k_stag_coef3(Layout L, const T* vel, const T* rho, const uint8_t* mp, const uint8_t* mv0,
+                             const uint8_t* mv1, const uint8_t* mv2, double dt, double inv_h, T* kp, T* b0, T* b1,
+                             T* b2) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < L.N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t x = i % L.nx, r = i / L.nx, y = r % L.ny, z = r / L.ny;
+        const int64_t q = L.idx(x, y, z);
+        const double r0 = rho ? (double)rho[i] : 1.0;
+        const double c = (double)vel[i];
+        kp[q] = mp[q] ? (T)(dt * r0 * c * c * inv_h) : (T)0;
+        const double rx = (rho && x + 1 < L.nx) ? (double)rho[i + 1] : r0;
+        const double ry = (rho && y + 1 < L.ny) ? (double)rho[i + L.nx] : r0;
+        const double rz = (rho && z + 1 < L.nz) ? (double)rho[i + L.nx * L.ny] : r0;
+        b0[q] = mv0[q] ? (T)(dt * 0.5 * (1.0 / r0 + 1.0 / rx) * inv_h) : (T)0;
+        b1[q] = mv1[q] ? (T)(dt * 0.5 * (1.0 / r0 + 1.0 / ry) * inv_h) : (T)0;
+        b2[q] = mv2[q] ? (T)(dt * 0.5 * (1.0 / r0 + 1.0 / rz) * inv_h) : (T)0;
+    }
+}
+
+template <typename T, int H>
+struct Stag3Args {
+    Layout L;
+    T c[4];              // c[k - 1]: weight of the pair at offsets +(k - 1/2), -(k - 1/2)
+    T* p;
+    T* v[3];
+    const T* kp;
+    const T* b[3];
+};
+
+// v_a += b_a (forward-staggered d/dx_a p) at every interior v_a node
+template <typename T, int H>
+__global__ void __launch_bounds__(256) k_stag_v3d(Stag3Args<T, H> a) {
+    const Layout& L = a.L;
+    const int64_t st[3] = {1, L.px, L.plane};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < L.N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t x = i % L.nx, r = i / L.nx, y = r % L.ny, z = r / L.ny;
+        const int64_t q = L.idx(x, y, z);
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax) {
+            const T bq = a.b[ax][q];
+            if (bq == (T)0) continue;
+            T s = 0;
+#pragma unroll
+            for (int k = 1; k <= H; ++k) s += a.c[k - 1] * (a.p[q + k * st[ax]] - a.p[q - (k - 1) * st[ax]]);
+            a.v[ax][q] += bq * s;
+        }
+    }
+}
+
+// p += kp (backward-staggered divergence of v) at every interior p node
+template <typename T, int H>
+__global__ void __launch_bounds__(256) k_stag_p3d(Stag3Args<T, H> a) {
+    const Layout& L = a.L;
+    const int64_t st[3] = {1, L.px, L.plane};
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < L.N; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t x = i % L.nx, r = i / L.nx, y = r % L.ny, z = r / L.ny;
+        const int64_t q = L.idx(x, y, z);
+        const T kq = a.kp[q];
+        if (kq == (T)0) continue;
+        T s = 0;
+#pragma unroll
+        for (int ax = 0; ax < 3; ++ax)
+#pragma unroll
+            for (int k = 1; k <= H; ++k)
+                s += a.c[k - 1] * (a.v[ax][q + (k - 1) * st[ax]] - a.v[ax][q - k * st[ax]]);
+        a.p[q] += kq * s;
+    }
+}
+
+// out[q] += coef[q] sum_j w_j f[q + col_j] over the rows of one operator, 8 lanes per
+// row (rows are distinct nodes within an operator; the sum is added by a reduction
+// that returns nothing)
+template <typename T>
+__global__ void __launch_bounds__(256) k_ib_rows(int64_t nrows, const int64_t* __restrict__ row_pad,
+                                                 const int64_t* __restrict__ row_ptr,
+                                                 const int64_t* __restrict__ col_pad, const T* __restrict__ w,
+                                                 const T* __restrict__ f, const T* __restrict__ coef, T* out) {
+    const int lane = threadIdx.x & 31, gl = lane & 7;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarp = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t rb = warp * 4; rb < nrows; rb += nwarp * 4) {
+        const int64_t r = rb + (lane >> 3);
+        const bool act = r < nrows;
+        const int64_t q = act ? row_pad[r] : 0;
+        const int64_t j1 = act ? row_ptr[r + 1] : 0;
+        T v = 0;
+        for (int64_t j = (act ? row_ptr[r] : 0) + gl; j < j1; j += 8) v += w[j] * f[q + col_pad[j]];
+        v += __shfl_xor_sync(0xffffffffu, v, 4, 8);
+        v += __shfl_xor_sync(0xffffffffu, v, 2, 8);
+        v += __shfl_xor_sync(0xffffffffu, v, 1, 8);
+        if (act && gl == 0) atomicAdd(&out[q], coef[q] * v);
+    }
+}
+
+// sources: p[corner] += w * wavelet[n] (weights include dt / h^d)
+template <typename T>
+__global__ void k_add_sources(PointSet<T> src, const T* wavelet, int n, T* p) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < 8 * src.n && src.w[i] != (T)0) atomicAdd(&p[src.idx[i]], src.w[i] * wavelet[n]);
+}
+
+template <typename T, int H>
+static ib_status stag3_steps(ib_table* t, const ib_shot* sh, int nt, Stag3Args<T, H>& a, const Geom<T>& g,
+                             cudaStream_t s) {
+    const Layout& L = a.L;
+    const int gb = grid1(L.N, 256);
+    for (int n = 0; n < nt; ++n) {
+        PROF_LAUNCH(kname<T>("stag_v3d_f32", "stag_v3d_f64"), s, { k_stag_v3d<T, H><<<gb, 256, 0, s>>>(a); });
+        for (int ax = 0; ax < 3; ++ax) {
+            const IbOp& op = t->ops[ax];
+            if (!op.nrows) continue;
+            const T* w = sizeof(T) == 8 ? (const T*)op.w64 : (const T*)op.w32;
+            PROF_LAUNCH(kname<T>("ib_rows3_f32", "ib_rows3_f64"), s, {
+                k_ib_rows<T><<<grid1(op.nrows * 8, 256), 256, 0, s>>>(op.nrows, op.row_pad, op.row_ptr, op.col_pad,
+                                                                       w, a.p, a.b[ax], a.v[ax]);
+            });
+        }
+        PROF_LAUNCH(kname<T>("stag_p3d_f32", "stag_p3d_f64"), s, { k_stag_p3d<T, H><<<gb, 256, 0, s>>>(a); });
+        for (int ax = 0; ax < 3; ++ax) {
+            const IbOp& op = t->ops[3 + ax];
+            if (!op.nrows) continue;
+            const T* w = sizeof(T) == 8 ? (const T*)op.w64 : (const T*)op.w32;
+            PROF_LAUNCH(kname<T>("ib_rows3_f32", "ib_rows3_f64"), s, {
+                k_ib_rows<T><<<grid1(op.nrows * 8, 256), 256, 0, s>>>(op.nrows, op.row_pad, op.row_ptr, op.col_pad,
+                                                                       w, a.v[ax], a.kp, a.p);
+            });
+        }
+        if (g.src.n) {
+            k_add_sources<T><<<1, 256, 0, s>>>(g.src, (const T*)sh->wavelet_dev, n, a.p);
+            ib_count_launch("setup");
+        }
+        if (g.rec.n) {
+            k_receivers<T><<<grid1(g.rec.n, 256), 256, 0, s>>>(g.rec, a.p, (T*)sh->traces_dev, nt, n);
+            ib_count_launch("setup");
+        }
+        IB_CHECK_LAUNCH("3D staggered step");
+    }
+    return IB_OK;
+}
+
+template <typename T>
+static ib_status forward_stag3(ib_table* t, const ib_shot* sh, double dt, int nt, cudaStream_t s) {
+    const Layout& L = t->L;
+    if (shot_damped(sh)) {
+        ib_set_error("the absorbing layer is implemented for the second-order form");
+        return IB_ERR_STATE;
+    }
+    const int M = t->opts.space_order;
+    const int H = M / 2;
+    Scratch S(s);
+    T *p, *v0, *v1, *v2, *kp, *b0, *b1, *b2;
+    TRY(S.alloc(&p, L.total, true));
+    TRY(S.alloc(&v0, L.total, true));
+    TRY(S.alloc(&v1, L.total, true));
+    TRY(S.alloc(&v2, L.total, true));
+    TRY(S.alloc(&kp, L.total, true));
+    TRY(S.alloc(&b0, L.total, true));
+    TRY(S.alloc(&b1, L.total, true));
+    TRY(S.alloc(&b2, L.total, true));
+    k_stag_coef3<T><<<grid1(L.N, 256), 256, 0, s>>>(L, (const T*)sh->vel_dev, (const T*)sh->rho_dev, t->mask_pad[0],
+                                                    t->mask_pad[1], t->mask_pad[2], t->mask_pad[3], dt,
+                                                    1.0 / t->grid.h, kp, b0, b1, b2);
+    IB_CHECK_LAUNCH("k_stag_coef3");
+    ib_count_launch("setup");
+    Geom<T> g;
+    TRY(setup_points<T>(t, sh, dt / pow(t->grid.h, 3), S, g));
+    T w2u[5], c1[4];
+    stencil_weights<T>(M, w2u, c1);
+    auto run = [&](auto hc) -> ib_status {
+        constexpr int HH = decltype(hc)::value;
+        Stag3Args<T, HH> a;
+        memset(&a, 0, sizeof a);
+        a.L = L;
+        for (int k = 0; k < 4; ++k) a.c[k] = c1[k];
+        a.p = p;
+        a.v[0] = v0;
+        a.v[1] = v1;
+        a.v[2] = v2;
+        a.kp = kp;
+        a.b[0] = b0;
+        a.b[1] = b1;
+        a.b[2] = b2;
+        return stag3_steps<T, HH>(t, sh, nt, a, g, s);
+    };
+    if (H == 1) TRY(run(std::integral_constant<int, 1>()));
+    else if (H == 2) TRY(run(std::integral_constant<int, 2>()));
+    else if (H == 3) TRY(run(std::integral_constant<int, 3>()));
+    else TRY(run(std::integral_constant<int, 4>()));
+    TRY(check_finite<T>(L.total, p, v0, v1, s));
+    TRY(check_finite<T>(L.total, v2, (const T*)nullptr, (const T*)nullptr, s));
+    return IB_OK;
+}
+
 extern "C" ib_status ib_forward(const ib_table* tc, const ib_shot* sh, int32_t precision, double dt, int32_t nt,
                                 void* ckpt, int32_t n_ckpt, void* stream) {
     ib_set_error("");
@@ -2527,6 +2730,8 @@ extern "C" ib_status ib_forward(const ib_table* tc, const ib_shot* sh, int32_t p
         ib_set_error("checkpoints are supported for the second-order form");
         return IB_ERR_STATE;
     }
+    if (t->grid.ndim == 3)
+        return precision == 64 ? forward_stag3<double>(t, sh, dt, nt, s) : forward_stag3<float>(t, sh, dt, nt, s);
     return precision == 64 ? forward_stag<double>(t, sh, dt, nt, s) : forward_stag<float>(t, sh, dt, nt, s);
 }
 
