@@ -62,6 +62,11 @@ typedef enum {
 } ib_status;
 
 typedef enum { IB_FREE = 0, IB_RIGID = 1 } ib_bc;
+/* How exterior values are extrapolated: the paper's N-dimensional Taylor basis
+ * over a hyperspherical support ("Approximating Boundary Conditions"), or the
+ * per-axis 1D extrapolation it derives as a sub-case ("Reduction to 1D"; the
+ * free surface of the second-order form only). */
+typedef enum { IB_EXTRAP_ND = 0, IB_EXTRAP_1D = 1 } ib_extrap;
 typedef enum { IB_SECOND_ORDER = 0, IB_FIRST_ORDER_STAGGERED = 1 } ib_form;
 
 typedef struct {
@@ -77,7 +82,16 @@ typedef struct {
                               (the reduced basis of the order-reduction paragraph;
                               M gives the consistent-error basis)                  */
     int32_t min_order;     /* lowest basis order of the fallback (>= 2)            */
-    int32_t reserved;
+    int32_t extrapolation; /* ib_extrap: IB_EXTRAP_ND (default) or IB_EXTRAP_1D.
+                              1D: on each grid line an axial stencil crosses the
+                              surface, the boundary is where the SDF, interpolated
+                              linearly between the last interior and the first
+                              exterior node, is zero; the 1D Taylor basis of order
+                              M (lowered by 2 while the line is too short) is fitted
+                              to the M/2 nearest nodes at more than eta_p from it
+                              and to p = p'' = .. = p^(M) = 0 there, a square
+                              system; basis_order, radius, growth and rank_tol
+                              do not apply                                         */
     double radius;         /* initial support radius in grid units; <= 0 ->
                               (basis_order + 1) / 2 (support paragraph)            */
     double growth;         /* radius grows by 0.5 up to radius + growth            */

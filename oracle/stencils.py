@@ -80,7 +80,7 @@ class RankError(RuntimeError):
 
 class Opts:
     def __init__(self, M, eta_p=None, eta_v=0.0, radius=0.0, growth=3.0,
-                 min_order=2, rank_tol=None, ib_order=0):
+                 min_order=2, rank_tol=None, ib_order=0, extrap="nd"):
         self.M = int(M)
         # basis order of the extrapolants (<= M); 0 selects min(M, 4) (see basis)
         self.ib_order = int(ib_order)
@@ -92,6 +92,11 @@ class Opts:
         self.min_order = int(min_order)
         # rank tolerance; None selects the default of for_bc
         self.rank_tol = None if rank_tol is None else float(rank_tol)
+        # "nd": N-dimensional basis over a hyperspherical support (the paper's
+        # method); "1d": per-axis 1D extrapolation (laplacian_rows_1d)
+        if extrap not in ("nd", "1d"):
+            raise ValueError("extrap must be 'nd' or '1d'")
+        self.extrap = extrap
 
     def for_bc(self, bc):
         """These options with the boundary-condition defaults filled in: rank
@@ -99,7 +104,7 @@ class Opts:
         out = Opts(self.M, eta_p=self.eta_pressure(bc), eta_v=self.eta_v, radius=self.radius,
                    growth=self.growth, min_order=self.min_order,
                    rank_tol=self.rank_tol if self.rank_tol is not None else (1e-3 if bc == "free" else 1e-2),
-                   ib_order=self.ib_order)
+                   ib_order=self.ib_order, extrap=self.extrap)
         return out
 
     def eta_pressure(self, bc):
@@ -297,6 +302,8 @@ def laplacian_rows(geom, bc, opts, nodes=None):
     Returns dict node -> (dict offset -> weight, info).
     """
     opts = opts.for_bc(bc)
+    if opts.extrap == "1d":
+        return laplacian_rows_1d(geom, bc, opts, nodes)
     M = opts.M
     w2 = [float(x) for x in taylor.central_second(M)]
     H = M // 2
@@ -321,6 +328,103 @@ def laplacian_rows(geom, bc, opts, nodes=None):
             off = tuple(jj - nn for jj, nn in zip(j, node))
             wts[off] = wts.get(off, 0.0) + float(cj)
         out[node] = (wts, info)
+    return out
+
+
+def extrapolation_1d(u_int, u_b, u_e, P, bc):
+    """Weights e (one per interior point) of the 1D extrapolant of order P at u_e:
+    f~(u_e) = sum_i e_i f(u_i).  Rows: the Taylor basis u^m / m! (m <= P) at the
+    interior points u_int, and its derivatives of the free-surface conditions
+    p = 0, p'' = 0, .. (orders 0, 2, .. <= P) at u_b with right-hand side zero
+    ("Reduction to 1D"); solved with the pseudoinverse (the inverse: the system
+    is square)."""
+    if bc != "free":
+        raise ValueError("the 1D reduction is stated for the free surface")
+    m = np.arange(P + 1)
+    fact = np.array([math.factorial(int(k)) for k in m], dtype=np.float64)
+    rows = [np.asarray(u, dtype=np.float64) ** m / fact for u in u_int]
+    for j in range(0, P + 1, 2):
+        r = np.zeros(P + 1)
+        for k in range(j, P + 1):
+            r[k] = u_b ** (k - j) / math.factorial(k - j)
+        rows.append(r)
+    A = np.array(rows)
+    phi_e = np.asarray(u_e, dtype=np.float64) ** m / fact
+    return (phi_e @ np.linalg.pinv(A))[:len(u_int)]
+
+
+def laplacian_rows_1d(geom, bc, opts, nodes=None):
+    """Modified-Laplacian corrections from per-axis 1D extrapolation, the variant
+    the paper relates to Mulder's scheme ("Reduction to 1D").  For each axis and
+    each side of an IB row's axial stencil that reaches in-array exterior nodes:
+    the boundary is where the SDF, interpolated linearly between the last
+    interior node and the first exterior node on that side, crosses zero (a
+    reading: the paper places 1D boundary points on the grid line without
+    saying how); the interior points are the P/2 nodes on the line, moving away
+    from the boundary, at more than eta from it, for a square system with the
+    P/2 + 1 conditions of order <= P; P = M, lowered by 2 while the line holds
+    too few such nodes.  Every exterior node of that side takes the
+    extrapolated value.  Corrections are summed over axes and sides.  Free
+    surface only: the paper states the reduction for p = 0, p'' = 0, ...
+    info: radius 0, order = the lowest P used."""
+    if bc != "free":
+        raise ValueError("the 1D reduction is stated for the free surface")
+    M = opts.M
+    H = M // 2
+    w2 = [float(x) for x in taylor.central_second(M)]
+    eta = opts.eta_pressure(bc)
+    sdf = geom.sdf_g
+    if nodes is None:
+        nodes = laplacian_ib_nodes(geom.mask, M)
+    out = {}
+    for node in nodes:
+        wts = {}
+        pmin = M
+        for a in range(geom.d):
+            for sg in (1, -1):
+                ext = []
+                for k in range(1, H + 1):
+                    nb = list(node)
+                    nb[a] += sg * k
+                    if in_array(nb, geom.lshape) and not value(geom.mask, nb):
+                        ext.append(k)
+                if not ext:
+                    continue
+                kb = ext[0]
+                n_in = list(node)
+                n_in[a] += sg * (kb - 1)
+                n_ex = list(node)
+                n_ex[a] += sg * kb
+                s1, s2 = value(sdf, n_in), value(sdf, n_ex)
+                u_b = (kb - 1) + s1 / (s1 - s2)
+                cand = []
+                u = kb - 1
+                while True:
+                    nb = list(node)
+                    nb[a] += sg * u
+                    if not in_array(nb, geom.lshape) or not value(geom.mask, nb):
+                        break
+                    if u_b - u > eta:
+                        cand.append(u)
+                    u -= 1
+                    if len(cand) > M:
+                        break
+                P = M
+                while P > 0 and len(cand) < P // 2:
+                    P -= 2
+                need = P // 2
+                pmin = min(pmin, P)
+                if need == 0:
+                    continue            # order 0: the extrapolant is zero
+                pts = cand[:need]
+                for k in ext:
+                    e = extrapolation_1d(pts, u_b, k, P, bc)
+                    for ui, ei in zip(pts, e):
+                        off = [0] * geom.d
+                        off[a] = sg * ui
+                        off = tuple(off)
+                        wts[off] = wts.get(off, 0.0) + w2[H + k] * float(ei)
+        out[node] = (wts, dict(radius=0.0, order=pmin, n_bp=0, cond=1.0))
     return out
 
 

@@ -1728,6 +1728,56 @@ struct FitKind {
 };
 
 // Build the fits of one kind and return the packed per-field CSR tables.
+// the fit results of the rows (pool entries per row, info) packed into the
+// table's CSR operators, one per field
+static ib_status pack_pool(ib_table* t, const FitKind& fk, const int64_t* rows, int64_t nrows, const int32_t* info,
+                           const int32_t* cnt, const int64_t* start, const int32_t* pool_code,
+                           const int8_t* pool_field, const double* pool_w, int op_first, cudaStream_t s,
+                           DevBuf& tmp) {
+    const Layout& L = t->L;
+    for (int f = 0; f < fk.nf; ++f) {
+        IbOp& op = t->ops[op_first + f];
+        op.nrows = nrows;
+        op.field_row = fk.rule.row_field;
+        op.field_col = fk.fkind[f];
+        int64_t *fc, *fptr;
+        TRY(tmp.alloc(&fc, nrows + 1));
+        TRY(dalloc(&op.row_ptr, nrows + 1));
+        IB_CUDA(cudaMemsetAsync(fc, 0, sizeof(int64_t) * (nrows + 1), s));
+        if (nrows) {
+            k_count_field<<<grid_for(nrows, 256), 256, 0, s>>>(nrows, cnt, start, pool_field, f, fc);
+            IB_CHECK_LAUNCH("k_count_field");
+            ib_count_launch("setup");
+        }
+        TRY(excl_scan(fc, op.row_ptr, nrows + 1, s));
+        fptr = op.row_ptr;
+        int64_t nnz = 0;
+        IB_CUDA(cudaMemcpy(&nnz, op.row_ptr + nrows, sizeof(int64_t), cudaMemcpyDeviceToHost));
+        op.nnz = nnz;
+        TRY(dalloc(&op.col_code, nnz));
+        TRY(dalloc(&op.col_pad, nnz));
+        TRY(dalloc(&op.w64, nnz));
+        TRY(dalloc(&op.w32, nnz));
+        TRY(dalloc(&op.row_lin, nrows));
+        TRY(dalloc(&op.row_pad, nrows));
+        TRY(dalloc(&op.row_info, 4 * nrows));
+        if (nrows) {
+            k_pack<<<grid_for(nrows, 32), 32, 0, s>>>(nrows, cnt, start, fptr, pool_code, pool_field, pool_w, f,
+                                                       fk.nf, op.col_code, op.w64, op.w32, op.col_pad, L, nullptr);
+            IB_CHECK_LAUNCH("k_pack");
+            ib_count_launch("setup");
+            IB_CUDA(cudaMemcpyAsync(op.row_lin, rows, sizeof(int64_t) * nrows, cudaMemcpyDeviceToDevice, s));
+            IB_CUDA(cudaMemcpyAsync(op.row_info, info, 16 * nrows, cudaMemcpyDeviceToDevice, s));
+            k_row_pad<<<grid_for(nrows, 256), 256, 0, s>>>(nrows, rows, L, op.row_pad);
+            IB_CHECK_LAUNCH("k_row_pad");
+            ib_count_launch("setup");
+        }
+        IB_CUDA(cudaStreamSynchronize(s));
+        t->table_bytes += nnz * (4 + 8 + 8 + 4) + nrows * (8 + 8 + 8 + 16);
+    }
+    return IB_OK;
+}
+
 static ib_status run_fit(ib_table* t, const Geo& g, const FitKind& fk, const int32_t* bp_index,
                          const double* bp_xb, const double* bp_n, int op_first, cudaStream_t s,
                          DevBuf& tmp) {
@@ -1920,47 +1970,226 @@ static ib_status run_fit(ib_table* t, const Geo& g, const FitKind& fk, const int
         }
     }
     // pack per field
-    for (int f = 0; f < fk.nf; ++f) {
-        IbOp& op = t->ops[op_first + f];
-        op.nrows = nrows;
-        op.field_row = fk.rule.row_field;
-        op.field_col = fk.fkind[f];
-        int64_t *fc, *fptr;
-        TRY(tmp.alloc(&fc, nrows + 1));
-        TRY(dalloc(&op.row_ptr, nrows + 1));
-        IB_CUDA(cudaMemsetAsync(fc, 0, sizeof(int64_t) * (nrows + 1), s));
-        if (nrows) {
-            k_count_field<<<grid_for(nrows, 256), 256, 0, s>>>(nrows, cnt, start, pool_field, f, fc);
-            IB_CHECK_LAUNCH("k_count_field");
-            ib_count_launch("setup");
+    return pack_pool(t, fk, rows, nrows, info, cnt, start, pool_code, pool_field, pool_w, op_first, s, tmp);
+}
+
+// ---------------------------------------------------------------------------
+// Per-axis 1D extrapolation ("Reduction to 1D": the paper's method with a 1D
+// basis on each grid line, the sub-case it relates to Mulder's scheme), free
+// surface.  One thread per IB row.  For each axis and each side of the row's
+// axial stencil that reaches in-array exterior nodes: the boundary is where the
+// SDF, interpolated linearly between the last interior node and the first
+// exterior node on that side, crosses zero; the interior points are the P/2
+// nodes on the line closest to it at more than eta; the 1D Taylor basis of order
+// P = M (lowered by 2 while the line holds too few such nodes) is fitted to them
+// and to p = 0, p'' = 0, .., p^(P) = 0 at the boundary (a square system, solved
+// by Gaussian elimination with partial pivoting in FP64); every exterior node of
+// that side takes the extrapolated value.  Entries go to row-owned pool slots.
+// ---------------------------------------------------------------------------
+#define FIT1D_MAXE 32
+
+struct Fit1dParams {
+    Geo g;
+    int M;
+    double eta;
+    double w2[9];           // central second-derivative weights, offsets -H .. H
+    const int64_t* rows;
+    int64_t nrows;
+    int32_t* info;          // [nrows][4]
+    int32_t* cnt;
+    int64_t* start;
+    int32_t* pool_code;
+    int8_t* pool_field;
+    double* pool_w;
+};
+
+// inverse of the (n x n) row-major matrix A (n <= 9) into Ai; false if singular
+__device__ bool small_inverse(double* A, double* Ai, int n) {
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) Ai[i * 9 + j] = i == j ? 1.0 : 0.0;
+    for (int c = 0; c < n; ++c) {
+        int piv = c;
+        for (int r = c + 1; r < n; ++r)
+            if (fabs(A[r * 9 + c]) > fabs(A[piv * 9 + c])) piv = r;
+        if (A[piv * 9 + c] == 0.0) return false;
+        if (piv != c)
+            for (int j = 0; j < n; ++j) {
+                double t = A[c * 9 + j];
+                A[c * 9 + j] = A[piv * 9 + j];
+                A[piv * 9 + j] = t;
+                t = Ai[c * 9 + j];
+                Ai[c * 9 + j] = Ai[piv * 9 + j];
+                Ai[piv * 9 + j] = t;
+            }
+        const double inv = 1.0 / A[c * 9 + c];
+        for (int j = 0; j < n; ++j) {
+            A[c * 9 + j] *= inv;
+            Ai[c * 9 + j] *= inv;
         }
-        TRY(excl_scan(fc, op.row_ptr, nrows + 1, s));
-        fptr = op.row_ptr;
-        int64_t nnz = 0;
-        IB_CUDA(cudaMemcpy(&nnz, op.row_ptr + nrows, sizeof(int64_t), cudaMemcpyDeviceToHost));
-        op.nnz = nnz;
-        TRY(dalloc(&op.col_code, nnz));
-        TRY(dalloc(&op.col_pad, nnz));
-        TRY(dalloc(&op.w64, nnz));
-        TRY(dalloc(&op.w32, nnz));
-        TRY(dalloc(&op.row_lin, nrows));
-        TRY(dalloc(&op.row_pad, nrows));
-        TRY(dalloc(&op.row_info, 4 * nrows));
-        if (nrows) {
-            k_pack<<<grid_for(nrows, 32), 32, 0, s>>>(nrows, cnt, start, fptr, pool_code, pool_field, pool_w, f,
-                                                       fk.nf, op.col_code, op.w64, op.w32, op.col_pad, L, nullptr);
-            IB_CHECK_LAUNCH("k_pack");
-            ib_count_launch("setup");
-            IB_CUDA(cudaMemcpyAsync(op.row_lin, rows, sizeof(int64_t) * nrows, cudaMemcpyDeviceToDevice, s));
-            IB_CUDA(cudaMemcpyAsync(op.row_info, info, 16 * nrows, cudaMemcpyDeviceToDevice, s));
-            k_row_pad<<<grid_for(nrows, 256), 256, 0, s>>>(nrows, rows, L, op.row_pad);
-            IB_CHECK_LAUNCH("k_row_pad");
-            ib_count_launch("setup");
+        for (int r = 0; r < n; ++r) {
+            if (r == c) continue;
+            const double f = A[r * 9 + c];
+            if (f == 0.0) continue;
+            for (int j = 0; j < n; ++j) {
+                A[r * 9 + j] -= f * A[c * 9 + j];
+                Ai[r * 9 + j] -= f * Ai[c * 9 + j];
+            }
         }
-        IB_CUDA(cudaStreamSynchronize(s));
-        t->table_bytes += nnz * (4 + 8 + 8 + 4) + nrows * (8 + 8 + 8 + 16);
     }
-    return IB_OK;
+    return true;
+}
+
+__global__ void __launch_bounds__(128) k_fit1d(Fit1dParams P) {
+    const Geo& g = P.g;
+    const int H = P.M / 2;
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < P.nrows;
+         r += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t lin = P.rows[r];
+        int64_t p[3] = {lin % g.n[0], 0, 0};
+        if (g.ndim == 2) {
+            p[1] = lin / g.n[0];
+        } else {
+            p[1] = (lin / g.n[0]) % g.n[1];
+            p[2] = lin / (g.n[0] * g.n[1]);
+        }
+        int32_t code[FIT1D_MAXE];
+        double wsum[FIT1D_MAXE];
+        int ne = 0;
+        int pmin = P.M;
+        bool bad = false;
+        for (int a = 0; a < g.ndim; ++a)
+            for (int sg = 1; sg >= -1; sg -= 2) {
+                unsigned ext = 0;
+                for (int k = 1; k <= H; ++k) {
+                    int64_t q[3] = {p[0], p[1], p[2]};
+                    q[a] += sg * k;
+                    if (in_arr(g, q) && !(sdf_at(g, q) > 0.0)) ext |= 1u << k;
+                }
+                if (!ext) continue;
+                const int kb = __ffs(ext) - 1;
+                int64_t qi[3] = {p[0], p[1], p[2]}, qe[3] = {p[0], p[1], p[2]};
+                qi[a] += sg * (kb - 1);
+                qe[a] += sg * kb;
+                const double s1 = sdf_at(g, qi), s2 = sdf_at(g, qe);
+                const double ub = (kb - 1) + s1 / (s1 - s2);
+                int cand[4];
+                int nc = 0;
+                for (int u = kb - 1; nc < H; --u) {
+                    int64_t q[3] = {p[0], p[1], p[2]};
+                    q[a] += sg * u;
+                    if (!in_arr(g, q) || !(sdf_at(g, q) > 0.0)) break;
+                    if (ub - u > P.eta) cand[nc++] = u;
+                }
+                int Pd = P.M;
+                while (Pd > 0 && nc < Pd / 2) Pd -= 2;
+                const int need = Pd / 2, n = Pd + 1;
+                pmin = min(pmin, Pd);
+                if (need == 0) continue;   // order 0: the extrapolant is zero
+                // rows: basis u^m / m! at the interior points, then the even derivatives at ub
+                double A[81], Ai[81], fact[9];
+                fact[0] = 1.0;
+                for (int m = 1; m < n; ++m) fact[m] = fact[m - 1] * m;
+                for (int i = 0; i < need; ++i) {
+                    double pw = 1.0;
+                    for (int m = 0; m < n; ++m) {
+                        A[i * 9 + m] = pw / fact[m];
+                        pw *= (double)cand[i];
+                    }
+                }
+                for (int jr = 0; jr <= Pd / 2; ++jr) {
+                    const int j = 2 * jr, row = need + jr;
+                    for (int m = 0; m < n; ++m) {
+                        if (m < j) {
+                            A[row * 9 + m] = 0.0;
+                        } else {
+                            double pw = 1.0;
+                            for (int e = 0; e < m - j; ++e) pw *= ub;
+                            A[row * 9 + m] = pw / fact[m - j];
+                        }
+                    }
+                }
+                if (!small_inverse(A, Ai, n)) {
+                    bad = true;
+                    continue;
+                }
+                for (int k = kb; k <= H; ++k) {
+                    if (!((ext >> k) & 1u)) continue;
+                    // e_i = sum_m phi_m(k) Ai[m][i]
+                    for (int i = 0; i < need; ++i) {
+                        double e = 0.0, pw = 1.0;
+                        for (int m = 0; m < n; ++m) {
+                            e += pw / fact[m] * Ai[m * 9 + i];
+                            pw *= (double)k;
+                        }
+                        int o[3] = {0, 0, 0};
+                        o[a] = sg * cand[i];
+                        const int32_t c = pack_off(o[0], o[1], o[2]);
+                        int slot = -1;
+                        for (int t = 0; t < ne; ++t)
+                            if (code[t] == c) slot = t;
+                        if (slot < 0 && ne < FIT1D_MAXE) {
+                            slot = ne++;
+                            code[slot] = c;
+                            wsum[slot] = 0.0;
+                        }
+                        if (slot >= 0) wsum[slot] += P.w2[H + k] * e;
+                    }
+                }
+            }
+        const int64_t st = r * FIT1D_MAXE;
+        P.start[r] = st;
+        P.cnt[r] = ne;
+        for (int t = 0; t < ne; ++t) {
+            P.pool_code[st + t] = code[t];
+            P.pool_field[st + t] = 0;
+            P.pool_w[st + t] = wsum[t];
+        }
+        P.info[4 * r + 0] = 0;
+        P.info[4 * r + 1] = pmin;
+        P.info[4 * r + 2] = 0;
+        P.info[4 * r + 3] = bad ? 1 : 0;
+    }
+}
+
+static ib_status run_fit1d(ib_table* t, const Geo& g, const FitKind& fk, int M, const std::vector<double>& w2,
+                           cudaStream_t s, DevBuf& tmp) {
+    const Layout& L = t->L;
+    uint8_t* flags = nullptr;
+    TRY(tmp.alloc(&flags, L.N));
+    k_row_flags<<<grid_for(L.N, 256), 256, 0, s>>>(g, fk.rule, flags);
+    IB_CHECK_LAUNCH("k_row_flags");
+    ib_count_launch("setup");
+    int64_t* rows = nullptr;
+    int64_t nrows = 0;
+    TRY(compact(flags, L.N, &rows, &nrows, s));
+    tmp.ptrs.push_back(rows);
+    Fit1dParams P;
+    memset(&P, 0, sizeof P);
+    P.g = g;
+    P.M = M;
+    P.eta = fk.feta[0];
+    for (int k = 0; k <= M && k < 9; ++k) P.w2[k] = w2[k];
+    P.rows = rows;
+    P.nrows = nrows;
+    const int64_t nr = std::max<int64_t>(nrows, 1);
+    TRY(tmp.alloc(&P.info, 4 * nr));
+    TRY(tmp.alloc(&P.cnt, nr));
+    TRY(tmp.alloc(&P.start, nr));
+    TRY(tmp.alloc(&P.pool_code, nr * FIT1D_MAXE));
+    TRY(tmp.alloc(&P.pool_field, nr * FIT1D_MAXE));
+    TRY(tmp.alloc(&P.pool_w, nr * FIT1D_MAXE));
+    if (nrows) {
+        k_fit1d<<<grid_for(nrows, 128), 128, 0, s>>>(P);
+        IB_CHECK_LAUNCH("k_fit1d");
+        ib_count_launch("setup");
+    }
+    std::vector<int32_t> hinfo(4 * nrows);
+    if (nrows) IB_CUDA(cudaMemcpy(hinfo.data(), P.info, 16 * nrows, cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < nrows; ++i) {
+        if (hinfo[4 * i + 3] != 0) t->n_fail++;
+        else if (hinfo[4 * i + 1] != M) t->n_reduced++;
+    }
+    return pack_pool(t, fk, rows, nrows, P.info, P.cnt, P.start, P.pool_code, P.pool_field, P.pool_w, 0, s, tmp);
 }
 
 static void free_op(IbOp& op) {
@@ -2028,6 +2257,14 @@ static ib_status build_impl(const ib_grid* grid, const double* sdf, ib_bc bc, ib
     if (o.eta_p < 0.0) o.eta_p = bc == IB_RIGID ? 0.25 : 0.5;
     if (bc != IB_FREE && bc != IB_RIGID) {
         ib_set_error("bc must be IB_FREE or IB_RIGID");
+        return IB_ERR_ARG;
+    }
+    if (o.extrapolation != IB_EXTRAP_ND && o.extrapolation != IB_EXTRAP_1D) {
+        ib_set_error("extrapolation must be IB_EXTRAP_ND or IB_EXTRAP_1D");
+        return IB_ERR_ARG;
+    }
+    if (o.extrapolation == IB_EXTRAP_1D && (form != IB_SECOND_ORDER || bc != IB_FREE || mlp)) {
+        ib_set_error("the 1D extrapolation is stated for the free surface of the second-order form");
         return IB_ERR_ARG;
     }
     if (form != IB_SECOND_ORDER && form != IB_FIRST_ORDER_STAGGERED) {
@@ -2116,7 +2353,11 @@ static ib_status build_impl(const ib_grid* grid, const double* sdf, ib_bc bc, ib
         fk.sdf = sdf;
         fk.accept_tol = accept_tol;
         t->nops = 1;
-        if ((st = run_fit(t, g, fk, bp_index, bp_xb, bp_n, 0, s, tmp)) != IB_OK) return fail(st);
+        if (o.extrapolation == IB_EXTRAP_1D)
+            st = run_fit1d(t, g, fk, M, w2, s, tmp);
+        else
+            st = run_fit(t, g, fk, bp_index, bp_xb, bp_n, 0, s, tmp);
+        if (st != IB_OK) return fail(st);
     } else {
         std::vector<double> c1 = ib_staggered_first(M);
         t->nops = 2 * d;

@@ -16,6 +16,7 @@ LIB_PATH = os.path.join(HERE, "libibwave.so")
 
 IB_OK, IB_ERR_ARG, IB_ERR_RANK, IB_ERR_CUDA, IB_ERR_OOM, IB_ERR_UNSTABLE, IB_ERR_TIMEOUT, IB_ERR_STATE = range(8)
 FREE, RIGID = 0, 1
+EXTRAP_ND, EXTRAP_1D = 0, 1
 SECOND_ORDER, FIRST_ORDER_STAGGERED = 0, 1
 
 EXPORTS = ["ib_opts_default", "ib_build_stencils", "ib_table_free", "ib_table_stats", "ib_table_export",
@@ -40,7 +41,7 @@ class Grid(ctypes.Structure):
 
 class Opts(ctypes.Structure):
     _fields_ = [("space_order", ctypes.c_int32), ("basis_order", ctypes.c_int32),
-                ("min_order", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("min_order", ctypes.c_int32), ("extrapolation", ctypes.c_int32),
                 ("radius", ctypes.c_double), ("growth", ctypes.c_double),
                 ("eta_p", ctypes.c_double), ("eta_v", ctypes.c_double),
                 ("rank_tol", ctypes.c_double)]

@@ -30,7 +30,7 @@ def gpu_rows(exp, shape, comp_prefix=None):
     return out
 
 
-def compare_tables(orc, gpu, rtol=1e-8, check_info=True):
+def compare_tables(orc, gpu, rtol=1e-8, check_info=True, floor=0.0):
     """Same IB nodes, same support sets, same radius and basis order, weights
     equal to (rtol + 1e-13 cond(A)) * max|w| of the row.  Returns the largest
     relative difference seen."""
@@ -45,7 +45,9 @@ def compare_tables(orc, gpu, rtol=1e-8, check_info=True):
         assert set(wo) == set(wg), (node, sorted(set(wo) ^ set(wg)))
         if not wo:
             continue
-        scale = max(1e-300, max(abs(v) for v in wo.values()))
+        # floor: the weight scale below which a row's corrections count as zero
+        # (rows whose corrections cancel analytically carry only rounding)
+        scale = max(1e-300, floor, max(abs(v) for v in wo.values()))
         d = max(abs(wo[k] - wg[k]) for k in wo) / scale
         worst = max(worst, d)
         # both sides carry rounding error ~ cond(A) * eps: allow 1e-13 * cond on top of rtol
