@@ -36,11 +36,11 @@ def _exact(bc, z0, xc=1.2, sig=0.15, s=0.15, k=2 * np.pi * 1.5):
     return sy.lambdify((x, z), u, "numpy"), sy.lambdify((x, z), f, "numpy")
 
 
-def _whole_field_error(M, P, bc, h, z0=0.35, Lx=2.4, Lz=1.55):
+def _whole_field_error(M, P, bc, h, z0=0.35, Lx=2.4, Lz=1.55, rank_tol=None):
     nx = int(round(Lx / h)) + 1
     nz = int(round(Lz / h)) + 1
     geom = stencils.Geometry(inputs.flat_surface_sdf((nx, nz), h, z0), h, M)
-    L, _ = operators.laplacian_matrix(geom, bc, stencils.Opts(M, ib_order=P))
+    L, _ = operators.laplacian_matrix(geom, bc, stencils.Opts(M, ib_order=P, rank_tol=rank_tol))
     uf, ff = _exact(bc, z0)
     X, Z = np.meshgrid(np.arange(nx) * h, np.arange(nz) * h)
     assert np.abs(uf(X, Z)[:, [0, -1]]).max() < 1e-25 and np.abs(uf(X, Z)[-1, :]).max() < 1e-25
@@ -51,8 +51,8 @@ def _whole_field_error(M, P, bc, h, z0=0.35, Lx=2.4, Lz=1.55):
     return float(np.abs(uh - u).max())
 
 
-def _orders(M, P, bc, hs):
-    e = [_whole_field_error(M, P, bc, h) for h in hs]
+def _orders(M, P, bc, hs, rank_tol=None):
+    e = [_whole_field_error(M, P, bc, h, rank_tol=rank_tol) for h in hs]
     return [float(np.log(a / b) / np.log(3.0)) for a, b in zip(e, e[1:])], e
 
 
@@ -74,10 +74,12 @@ def test_whole_field_order8_basis4(bc):
 
 @pytest.mark.parametrize("bc,bound", [("free", 8 - 0.7), ("rigid", 8 - 1.5)])
 def test_whole_field_order8_basis8(bc, bound):
-    """Order-8 interior and basis (ib_order = M): free >= 8 - 0.7
-    (measured 8.39); rigid >= 8 - 1.5 (measured 7.39, then 6.69 on the next
-    refinement: the rigid hierarchy imposes M/2 conditions per boundary
-    point, the free one M/2 + 1)."""
-    o, e = _orders(8, 8, bc, (1 / 30, 1 / 90))
+    """Order-8 interior and basis (ib_order = M) at rank tolerance 1e-3:
+    free >= 8 - 0.7 (measured 8.39); rigid >= 8 - 1.5 (measured 7.39, then
+    6.69 on the next refinement: the rigid hierarchy imposes M/2 conditions
+    per boundary point, the free one M/2 + 1).  The rigid default tolerance
+    (1e-2, chosen for the stability of the order-4 basis) rejects the order-8
+    fits of some rows near this surface and reduces them to order 4: 3.55."""
+    o, e = _orders(8, 8, bc, (1 / 30, 1 / 90), rank_tol=1e-3)
     assert all(x >= bound for x in o), (o, e)
     assert e[-1] < 1e-6 * 10, e
