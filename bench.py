@@ -45,7 +45,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="hills3d",
-                    choices=["stag2d", "hills3d", "flat2d", "batch2d", "adjoint2d", "learned3d"])
+                    choices=["stag2d", "hills3d", "flat2d", "batch2d", "adjoint2d", "learned3d", "tb2d"])
     ap.add_argument("--train-topos", type=int, default=24, help="learned3d: training topographies")
     ap.add_argument("--epochs", type=int, default=8, help="learned3d: training epochs")
     ap.add_argument("--accept-tol", type=float, default=1e-6, help="learned3d: exactness threshold")
@@ -53,7 +53,7 @@ def parse():
     ap.add_argument("--bc", default="free", choices=["free", "rigid"])
     ap.add_argument("--nt", type=int, default=0, help="override time steps (testing only)")
     ap.add_argument("--grid", type=int, nargs="*", default=None,
-                    help="override the grid (nx ny nz) of hills3d (profiling of smaller cases)")
+                    help="override the grid of hills3d (nx ny nz) or tb2d (nx nz) (profiling of smaller cases)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="time the chosen workload only")
@@ -533,6 +533,101 @@ def run_single(args, workload, steps, warmup, world, rank, local, dev, dist, wit
     }
 
 
+TB_GRID = (8192, 4096)
+
+
+def run_temporal(args, steps, warmup, world, rank, local, dev, dist, grid=None, nt=None):
+    """2D second-order FP32 shot, 8192 x 4096 nodes (h = 5 m, order 8,
+    sinusoid free surface, 4 layers, 400 steps): the forward call with one
+    leapfrog step per launch and with two (IB_TEMPORAL_BLOCK=1), table built
+    once outside the timed region, L2 flushed between calls.  The two-step
+    kernel moves 20 B per point per launch (p^n, p^{n-1}, K read, p^{n+1},
+    p^{n+2} written), 10 B per point and step against the 16 B of one step
+    per launch; its effective rate (16 B per point and step over its time) can
+    exceed the copy bandwidth and is reported beside the DRAM figure."""
+    import torch
+    from paper_2309_03600_gb300 import ib, inputs
+    nx, nz = grid or TB_GRID
+    h, M, nt = 5.0, 8, nt or 400
+    sdf = torch.as_tensor(inputs.sinusoid_sdf(nx, nz, h, device=dev), dtype=torch.float64, device=dev).contiguous()
+    vel = torch.as_tensor(inputs.layered_velocity((nx, nz), h, [800.0, 2000.0, 4000.0],
+                                                  [1500.0, 2200.0, 3000.0, 4000.0]), dtype=torch.float32, device=dev)
+    dt = inputs.dt_from_courant(0.4, h, 4000.0)
+    wav = torch.as_tensor(inputs.ricker(12.0, dt, nt), dtype=torch.float32, device=dev)
+    src = torch.tensor([[nx * h / 2, 600.0 + 1000.0 * rank]], dtype=torch.float64, device=dev)
+    rx = np.arange(10, nx - 10, 8) * h
+    rec = torch.as_tensor(np.stack([rx, np.full_like(rx, 400.0)], 1), device=dev)
+    tab = ib.ib_build_stencils(sdf, h, "free", "second", M)
+    stats = tab.stats()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    traces = torch.zeros((rec.shape[0], nt), dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    N = nx * nz
+    peak, peak_kind = peaks()
+    out = {}
+    old = os.environ.get("IB_TEMPORAL_BLOCK")
+    try:
+        for mode in ("one_step", "two_step"):
+            os.environ["IB_TEMPORAL_BLOCK"] = "1" if mode == "two_step" else "0"
+            for _ in range(warmup):
+                flush.zero_()
+                ib.ib_forward(tab, vel, wav, src, rec, dt, nt, traces=traces)
+            torch.cuda.synchronize()
+            ib.ib_profile_enable(8)
+            if dist:
+                dist.barrier()
+            torch.cuda.synchronize()
+            ev = []
+            for _ in range(steps):
+                flush.zero_()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                ib.ib_forward(tab, vel, wav, src, rec, dt, nt, traces=traces)
+                e1.record(stream)
+                ev.append((e0, e1))
+            torch.cuda.synchronize()
+            prof = ib.ib_profile()
+            ib.ib_profile_enable(0)
+            ib.ib_sync_status()
+            if not bool(torch.isfinite(traces).all()):
+                raise RuntimeError("non-finite traces in the two-step measurement")
+            ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / len(ev), dist, dev)
+            r = {"value": job_value(world, N * nt, ms), "ms_per_call": ms, "kernels": kernel_table(prof),
+                 "gpu_launches": int(sum(d["launches"] for d in prof.values()))}
+            if mode == "two_step":
+                k = prof.get("leap2d_tb2_f32")
+                if k and k["sampled"]:
+                    t = k["sampled_ms"] / k["sampled"] * 1e-3
+                    ach = 20.0 * N / t / 1e9
+                    r["roofline"] = {"bound": "hbm", "kernel": "leap2d_tb2_f32", "achieved": ach, "peak": peak,
+                                     "peak_kind": peak_kind, "unit": "GB/s", "frac": ach / peak,
+                                     "algorithmic_bytes_per_launch": 20.0 * N, "avg_launch_us": t * 1e6,
+                                     "traffic": dram_traffic("leap2d_tb2_f32"),
+                                     "effective_GBs_16B_per_point_step": 32.0 * N / t / 1e9,
+                                     "effective_frac": 32.0 * N / t / 1e9 / peak}
+            else:
+                kb = {"leap2d_strip_f32": 16.0 * N + ENTRY_BYTES[4] * sum(stats["nnz"]),
+                      "leap2d_f32": 16.0 * N + ENTRY_BYTES[4] * sum(stats["nnz"])}
+                r["roofline"] = roofline_of(prof, kb, peak, peak_kind)
+            out[mode] = r
+    finally:
+        if old is None:
+            os.environ.pop("IB_TEMPORAL_BLOCK", None)
+        else:
+            os.environ["IB_TEMPORAL_BLOCK"] = old
+    if rank != 0:
+        return None
+    return {"value": out["two_step"]["value"], "ms_per_step": out["two_step"]["ms_per_call"],
+            "config": {"workload": "tb2d", "grid": [nx, nz], "nt": nt, "space_order": M, "bc": "free",
+                       "desc": "2D second-order FP32, %dx%d, h=5 m, order 8, %d steps, sinusoid free "
+                               "surface, 4 layers; forward call only (table prebuilt)" % (nx, nz, nt),
+                       "ib_rows": stats["rows"], "ib_nnz": stats["nnz"], "l2": "flushed between calls"},
+            "one_step": out["one_step"], "two_step": out["two_step"],
+            "speedup_two_step": out["one_step"]["ms_per_call"] / out["two_step"]["ms_per_call"],
+            "gpu_launches": out["one_step"]["gpu_launches"] + out["two_step"]["gpu_launches"]}
+
+
 def main():
     args = parse()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -554,6 +649,15 @@ def main():
         dist.init_process_group("nccl", device_id=dev)
     if args.workload == "learned3d":
         return run_learned(args, world, rank, local, dev, dist)
+    if args.workload == "tb2d":   # the one-step / two-step comparison alone
+        r = run_temporal(args, args.steps, args.warmup, world, rank, local, dev, dist,
+                         tuple(args.grid) if args.grid else None, args.nt or None)
+        if rank == 0:
+            print(json.dumps(dict(metric=METRIC, unit=UNIT, n_gpus=world, steps=args.steps, warmup=args.warmup,
+                                  higher_is_better=True, dtype="f32", data="synthetic", **r)))
+        if dist:
+            dist.destroy_process_group()
+        return 0
     if args.workload in ("batch2d", "adjoint2d"):
         res = run_shots(args, args.workload, args.steps, args.warmup, world, rank, local, dev, dist)
     else:
@@ -571,6 +675,9 @@ def main():
             if r is not None:
                 extras[name] = {k: r[k] for k in ("value", "ms_per_step", "config", "setup", "roofline", "kernels",
                                                   "compare", "clocks", "gpu_launches") if k in r}
+        r = run_temporal(args, ex_steps, max(3, args.warmup), world, rank, local, dev, dist)
+        if r is not None:
+            extras["tb2d"] = r
     if rank != 0:
         if dist:
             dist.destroy_process_group()

@@ -992,9 +992,10 @@ __global__ void __launch_bounds__(256, D <= 2 ? 6 : 5) k_leap3d_tma(StepArgs<flo
 //   out[q] += (1 - g(q)) K[q] sum_j w_j p[q + off_j]
 // (g the absorbing-layer factor of the step, 0 outside the layer), entries as a
 // 16-bit footprint code and an FP32 weight in row order.  A group of 8 lanes takes
-// one row (a warp four rows), each lane up to four entries per round with their
+// one row (a warp four rows), each lane up to U entries per round with their
 // gathers in flight together, and the sum is added with a reduction that returns
 // nothing (rows are distinct nodes), so no lane waits on it.
+template <int U>
 __global__ void __launch_bounds__(256) k_ib_add3(int64_t nrows, const int64_t* __restrict__ row_pad,
                                                  const int64_t* __restrict__ row_ptr,
                                                  const uint16_t* __restrict__ code, const float* __restrict__ w,
@@ -1012,10 +1013,10 @@ __global__ void __launch_bounds__(256) k_ib_add3(int64_t nrows, const int64_t* _
         const int64_t q = act ? row_pad[r] : 0;
         const int64_t j0 = act ? row_ptr[r] : 0, j1 = act ? row_ptr[r + 1] : 0;
         float v = 0.f;
-        for (int64_t j = j0 + gl; j < j1; j += 32) {
-            float wv[4], pv[4];
+        for (int64_t j = j0 + gl; j < j1; j += 8 * U) {
+            float wv[U], pv[U];
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
+            for (int u = 0; u < U; ++u) {
                 const int64_t e = j + 8 * u;
                 const bool ok = e < j1;
                 const int c = ok ? code[e] : 16 | (16 << 5) | (16 << 10);
@@ -1023,7 +1024,7 @@ __global__ void __launch_bounds__(256) k_ib_add3(int64_t nrows, const int64_t* _
                 pv[u] = gather(q, c);
             }
 #pragma unroll
-            for (int u = 0; u < 4; ++u) v += wv[u] * pv[u];
+            for (int u = 0; u < U; ++u) v += wv[u] * pv[u];
         }
         v += __shfl_xor_sync(0xffffffffu, v, 4, 8);
         v += __shfl_xor_sync(0xffffffffu, v, 2, 8);
@@ -1065,6 +1066,247 @@ static void launch_leap3d_tma(const StepArgs<float>& a, const CUtensorMap& tm, c
         k_leap3d_tma<H, 5><<<grid, blk, sm, s>>>(a, tm, tmm, tmk, rw, zchunk, nty, err);
     } else {
         k_leap3d_tma<H, 3><<<grid, blk, tma3d_smem<H, 3>(), s>>>(a, tm, tmm, tmk, rw, zchunk, nty, err);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 3D step on x-pairs: the 64 x 8 column tile of a block is marched in z two
+// planes per iteration like k_leap3d_tma, with each thread computing two
+// x-adjacent points.  The x and y neighbours of the pair come in as 8-byte
+// shared-memory loads (the x row -4 .. +5 in five, each y neighbour pair in one)
+// and the waits, barriers and address arithmetic of an iteration are shared by
+// four points instead of two.  The corrections are added by k_ib_add3 after the
+// launch; sources touch shared memory only in the blocks that hold one.
+// ---------------------------------------------------------------------------
+template <int H, int D>
+struct Tma3P {
+    static constexpr int TX = 64, TY = 8;
+    static constexpr int BW = TX + 8;         // x halo 4 on each side (16-byte aligned box)
+    static constexpr int BH = TY + 2 * H;
+    static constexpr int NS = H + 1 + D;      // ring slots: planes z .. z + H + D
+    static constexpr int PF = (BW * BH + 31) / 32 * 32;   // p plane, padded to 128 bytes
+    static constexpr int TF = TX * TY;
+    static constexpr int SLOT = PF + 2 * TF;
+};
+
+// Laplacians of the pair centred at r0[0], r0[1] (r0 8-byte aligned, rows of 72
+// floats), z neighbours from the register queue q (centre q[H + O]); the grouping
+// and rounding of lap3_tma for each point
+template <int H, int O>
+__device__ __forceinline__ float2 lap3_pair(const float* r0, const float2 (&q)[2 * H + 2], const float* w2) {
+    constexpr int BW = 72;
+    float2 xv[5];   // r0[-4 .. 5]
+#pragma unroll
+    for (int j = 0; j < 5; ++j) xv[j] = *reinterpret_cast<const float2*>(r0 + 2 * j - 4);
+    auto X = [&](int o) -> float {
+        const int j = o + 4;
+        return (j & 1) ? xv[j >> 1].y : xv[j >> 1].x;
+    };
+    const float2 c = q[H + O];
+    const float c6a = __fmul_rn(6.f, c.x), c6b = __fmul_rn(6.f, c.y);
+    float sa = 0.f, sb = 0.f;
+#pragma unroll
+    for (int k = 1; k <= H; ++k) {
+        const float2 yp = *reinterpret_cast<const float2*>(r0 + k * BW);
+        const float2 ym = *reinterpret_cast<const float2*>(r0 - k * BW);
+        const float ga = __fadd_rn(__fadd_rn(__fadd_rn(X(k), X(-k)), __fadd_rn(yp.x, ym.x)),
+                                   __fadd_rn(q[H + O + k].x, q[H + O - k].x));
+        const float gb = __fadd_rn(__fadd_rn(__fadd_rn(X(1 + k), X(1 - k)), __fadd_rn(yp.y, ym.y)),
+                                   __fadd_rn(q[H + O + k].y, q[H + O - k].y));
+        sa = fmaf(w2[k], __fsub_rn(ga, c6a), sa);
+        sb = fmaf(w2[k], __fsub_rn(gb, c6b), sb);
+    }
+    return make_float2(sa, sb);
+}
+
+template <int H, int D>
+__global__ void __launch_bounds__(256, 3) k_leap3d_tma2(StepArgs<float> a, const __grid_constant__ CUtensorMap tm,
+                                                        const __grid_constant__ CUtensorMap tmm,
+                                                        const __grid_constant__ CUtensorMap tmk, int zchunk,
+                                                        int* err) {
+    using C = Tma3P<H, D>;
+    constexpr int TX = C::TX, TY = C::TY, BW = C::BW, NS = C::NS, SLOT = C::SLOT, PF = C::PF, TF = C::TF;
+    static_assert(NS >= H + 2, "planes z .. z + H + 1 are resident together");
+    static_assert(BW == 72 && H <= 4, "lap3_pair reads rows of 72 floats, x halo 4");
+    extern __shared__ __align__(128) float dsm[];
+    float* ring = dsm;                                  // NS * SLOT
+    float* sadd = ring + NS * SLOT;                     // [2][TY * TX]
+    uint64_t* bar = (uint64_t*)(sadd + 2 * TY * TX);    // NS
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * 32 + tx;
+    const int64_t blk = ((int64_t)blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
+    record_receivers(a.rec, a.p, a.traces, a.nt, a.rec_step, blk * 256 + tid, launch_threads());
+    const Layout& L = a.L;
+    const int64_t x0 = (int64_t)blockIdx.x * TX, y0 = (int64_t)blockIdx.y * TY;
+    const int64_t xa = x0 + 2 * tx, y = y0 + ty;        // this thread's points: (xa, y), (xa + 1, y)
+    const int64_t zb = (int64_t)blockIdx.z * zchunk;
+    const int64_t ze = min(zb + zchunk, L.nz);
+    const int64_t zlast = ze - 1 + H;
+    const bool va = xa < L.nx && y < L.ny, vb = xa + 1 < L.nx && y < L.ny;
+    const bool damped_xy = damp_box(L, a.dw, x0, x0 + TX - 1, y0, y0 + TY - 1, 0);
+    auto prow = [&](int64_t z) { return (int)((H + 1 + z) * L.py + y0); };
+    auto issue = [&](int slot, int64_t zz) {
+        const bool upd = zz < ze;
+        mbar_expect_tx(&bar[slot], (uint32_t)(BW * C::BH * 4 + (upd ? 2 * TF * 4 : 0)));
+        float* dst = ring + slot * SLOT;
+        tma_load_2d(dst, &tm, (int)(x0 - 4), prow(zz), &bar[slot]);
+        if (upd) {
+            tma_load_2d(dst + PF, &tmm, (int)x0, prow(zz) + H, &bar[slot]);
+            tma_load_2d(dst + PF + TF, &tmk, (int)x0, prow(zz) + H, &bar[slot]);
+        }
+    };
+    auto wait_plane = [&](int64_t zz) {
+        const int ip = (int)(zz - zb);
+        return mbar_wait_bounded(&bar[ip % NS], (uint32_t)((ip / NS) & 1));
+    };
+    if (tid == 0) {
+        for (int i = 0; i < NS; ++i) mbar_init(&bar[i], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    // does a source corner fall in this block's columns and z chunk? (block-uniform)
+    int src_here = 0;
+    const float wv = a.src.n ? a.wavelet[a.step] : 0.f;
+    const bool src_me = tid < 8 * a.src.n;
+    int64_t s_rel = -1;   // this thread's corner, relative to node (x0, y0, zb)
+    float s_val = 0.f;
+    if (src_me && a.src.w[tid] != 0.f) {
+        const int64_t rel = a.src.idx[tid] - L.idx(x0, y0, zb);
+        if (rel >= 0) {
+            const int64_t lz = rel / L.plane, r2 = rel - lz * L.plane;
+            const int64_t ly = r2 / L.px, lx = r2 - ly * L.px;
+            if (lz < ze - zb && ly < TY && lx < TX) {
+                s_rel = rel;
+                s_val = a.src.w[tid] * wv;
+            }
+        }
+    }
+    src_here = __syncthreads_or(s_rel >= 0);
+    if (tid == 0)
+        for (int i = 0; i < NS && zb + i <= zlast; ++i) issue(i, zb + i);
+    float2 q[2 * H + 2];
+    {
+        const bool ca = xa < L.nx + H && y < L.ny + H, cb = xa + 1 < L.nx + H && y < L.ny + H;
+#pragma unroll
+        for (int k = 0; k < 2 * H; ++k) {
+            const int64_t i = L.idx(xa, y, zb - H + k);
+            q[k] = make_float2(ca ? a.p[i] : 0.f, cb ? a.p[i + 1] : 0.f);
+        }
+    }
+    int64_t qi = L.idx(xa, y, zb);
+    const int ci = (H + ty) * BW + 4 + 2 * tx;   // pair centre in a slot's p plane
+    const int ti = ty * TX + 2 * tx;             // pair in a slot's p_prev / K tile
+    for (int64_t z = zb; z < ze; z += 2) {
+        const bool two = z + 1 < ze;
+        const int ia = (int)(z - zb);
+        bool ok = wait_plane(z) && wait_plane(z + H);
+        if (two) ok = ok && wait_plane(z + 1) && wait_plane(z + 1 + H);
+        // (after a failed wait the reads below see stale shared memory; the barrier
+        // that follows them tells every thread, and the block leaves)
+        const float* ra = ring + (ia % NS) * SLOT;
+        const float* rb = ring + ((ia + 1) % NS) * SLOT;
+        q[2 * H] = *reinterpret_cast<const float2*>(ring + ((ia + H) % NS) * SLOT + ci);
+        q[2 * H + 1] = two ? *reinterpret_cast<const float2*>(ring + ((ia + H + 1) % NS) * SLOT + ci)
+                           : make_float2(0.f, 0.f);
+        const float2 pma = *reinterpret_cast<const float2*>(ra + PF + ti);
+        const float2 kha = *reinterpret_cast<const float2*>(ra + PF + TF + ti);
+        const float2 pmb = *reinterpret_cast<const float2*>(rb + PF + ti);
+        const float2 khb = *reinterpret_cast<const float2*>(rb + PF + TF + ti);
+        const float2 la = lap3_pair<H, 0>(ra + ci, q, a.w2);
+        const float2 lb = lap3_pair<H, 1>(rb + ci, q, a.w2);
+        if (__syncthreads_or(!ok)) {
+            if (tid == 0) {
+                atomicExch(err, 1);
+                const int64_t ziss = min(z + NS - 1, zlast);
+                for (int64_t zp = z; zp <= ziss; ++zp) wait_plane(zp);
+            }
+            return;
+        }
+        // the two slots are free: the planes NS further into them
+        if (tid == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            if (z + NS <= zlast) issue(ia % NS, z + NS);
+            if (two && z + 1 + NS <= zlast) issue((ia + 1) % NS, z + 1 + NS);
+        }
+        float2 ua, ub;
+        ua.x = q[H].x + ((q[H].x - pma.x) + kha.x * la.x);
+        ua.y = q[H].y + ((q[H].y - pma.y) + kha.y * la.y);
+        ub.x = q[H + 1].x + ((q[H + 1].x - pmb.x) + khb.x * lb.x);
+        ub.y = q[H + 1].y + ((q[H + 1].y - pmb.y) + khb.y * lb.y);
+        if (src_here) {   // block-uniform
+            float2* s2 = reinterpret_cast<float2*>(sadd);
+            s2[tid] = make_float2(0.f, 0.f);
+            s2[TX * TY / 2 + tid] = make_float2(0.f, 0.f);
+            __syncthreads();
+            if (s_rel >= 0) {
+                const int64_t r = s_rel - (z - zb) * L.plane;
+                if (r >= 0) {
+                    const int64_t lz = r / L.plane, r2 = r - lz * L.plane;
+                    const int64_t ly = r2 / L.px, lx = r2 - ly * L.px;
+                    if (lz < (two ? 2 : 1)) atomicAdd(&sadd[lz * TX * TY + ly * TX + lx], s_val);
+                }
+            }
+            __syncthreads();
+            const float2 sa = s2[ti / 2], sb = s2[TX * TY / 2 + ti / 2];
+            ua.x += sa.x;
+            ua.y += sa.y;
+            ub.x += sb.x;
+            ub.y += sb.y;
+        }
+        if (damped_xy || (a.dw && z + 1 > L.nz - 1 - a.dw)) {
+            ua.x -= damp_g<float>(L, a.dw, a.da, xa, y, z) * (ua.x - pma.x);
+            ua.y -= damp_g<float>(L, a.dw, a.da, xa + 1, y, z) * (ua.y - pma.y);
+            if (two) {
+                ub.x -= damp_g<float>(L, a.dw, a.da, xa, y, z + 1) * (ub.x - pmb.x);
+                ub.y -= damp_g<float>(L, a.dw, a.da, xa + 1, y, z + 1) * (ub.y - pmb.y);
+            }
+        }
+        if (va && vb) {
+            *reinterpret_cast<float2*>(a.out + qi) = ua;
+            if (two) *reinterpret_cast<float2*>(a.out + qi + L.plane) = ub;
+        } else if (va) {
+            a.out[qi] = ua.x;
+            if (two) a.out[qi + L.plane] = ub.x;
+        }
+        qi += 2 * L.plane;
+#pragma unroll
+        for (int k = 0; k < 2 * H; ++k) q[k] = q[k + 2];
+    }
+    bool ok = true;
+    for (int64_t zz = ze; zz <= zlast; ++zz) ok = ok && wait_plane(zz);
+    if (!ok && tid == 0) atomicExch(err, 1);
+}
+
+template <int H, int D>
+static size_t tma3p_smem() {
+    using C = Tma3P<H, D>;
+    return sizeof(float) * ((size_t)C::NS * C::SLOT + 2 * C::TX * C::TY) + sizeof(uint64_t) * C::NS;
+}
+
+// x-pair kernel: 3 planes in flight beyond the ones read (IB_RING=2: 2).  At
+// 512^2 x 384, order 8: 325 us per launch with 3, 383 us with 2 (three blocks of
+// 74 KB or 65 KB per SM either way).
+template <int H>
+static void launch_leap3d_tma2(const StepArgs<float>& a, const CUtensorMap& tm, const CUtensorMap& tmm,
+                               const CUtensorMap& tmk, int zchunk, int* err, dim3 grid, cudaStream_t s) {
+    static const int ring = [] {
+        const char* e = getenv("IB_RING");
+        return e && atoi(e) == 2 ? 2 : 3;
+    }();
+    const dim3 blk(32, 8);
+    if (ring == 3) {
+        static const size_t sm = tma3p_smem<H, 3>();
+        static const bool attr = (cudaFuncSetAttribute(k_leap3d_tma2<H, 3>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
+                                  true);
+        (void)attr;
+        k_leap3d_tma2<H, 3><<<grid, blk, sm, s>>>(a, tm, tmm, tmk, zchunk, err);
+    } else {
+        static const size_t sm = tma3p_smem<H, 2>();
+        static const bool attr = (cudaFuncSetAttribute(k_leap3d_tma2<H, 2>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
+                                  true);
+        (void)attr;
+        k_leap3d_tma2<H, 2><<<grid, blk, sm, s>>>(a, tm, tmm, tmk, zchunk, err);
     }
 }
 
@@ -1859,12 +2101,14 @@ static bool tma_enabled() {
     return tma_encode_fn() != nullptr && !(e && e[0] == '1');
 }
 
-// 2D view of a padded FP32 3D field: rows of px elements; box (32 + 8) x (8 + 2H)
-// (a plane with its halo) or, with tile_only, 32 x 8 (a tile without halo)
-static ib_status make_plane_map(CUtensorMap& tm, void* base, const Layout& L, bool tile_only = false) {
+// 2D view of a padded FP32 3D field: rows of px elements; box (tw + 8) x (8 + 2H)
+// (a plane of a tile tw wide with its halo) or, with tile_only, tw x 8 (a tile
+// without halo)
+static ib_status make_plane_map(CUtensorMap& tm, void* base, const Layout& L, bool tile_only = false,
+                                uint32_t tw = 32) {
     cuuint64_t dims[2] = {(cuuint64_t)L.px, (cuuint64_t)(L.total / L.px)};
     cuuint64_t strides[1] = {(cuuint64_t)L.px * 4};
-    cuuint32_t box[2] = {tile_only ? 32u : 32u + 8u, tile_only ? 8u : (cuuint32_t)(8 + 2 * L.H)};
+    cuuint32_t box[2] = {tile_only ? tw : tw + 8u, tile_only ? 8u : (cuuint32_t)(8 + 2 * L.H)};
     cuuint32_t estr[2] = {1, 1};
     CUresult r = tma_encode_fn()(&tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, base, dims, strides, box, estr,
                                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -1991,6 +2235,387 @@ static void launch_leap2d_strip(const StepArgs<float>& a, int H, dim3 grid, cuda
     });
 }
 
+// ---------------------------------------------------------------------------
+// Temporal blocking: two leapfrog steps per launch (2D, second order, FP32).
+//
+// A block owns a TX x TZ output tile.  It stages p^n on the tile grown by 2R
+// ("region 2"), computes p^{n+1} on the tile grown by R ("region 1": standard
+// stencil, the immersed-boundary rows that lie there, source, absorbing
+// layer) and keeps it in shared memory, then computes p^{n+2} on the tile from
+// it.  R >= M/2 and R >= the reach of every correction row, so both steps read
+// shared memory only.  The ring of region 1 outside the tile is computed by the
+// neighbouring blocks as well: 2 x (1 + 2R/TX)(1 + 2R/TZ)/2 stencils per point
+// and step instead of 1, for DRAM traffic of p^n, p^{n-1}, K read and p^{n+1},
+// p^{n+2} written per two steps (20 bytes per point, 10 per point and step,
+// against 16 for one step per launch).  Outputs go to two further buffers:
+// the neighbours still read p^n and p^{n-1} in their halos.
+//
+// Correction entries of a tile: every row in region 1, those inside the tile
+// first (used by both steps), one int32 code per entry -- the row's position
+// in region 1 (x, z: 8 bits each) and the column offset (dx, dz: int8 each) --
+// and the FP32 weight.
+// ---------------------------------------------------------------------------
+struct TbArgs {
+    Layout L;
+    float w2[5];
+    const float* pn;         // p^n
+    const float* pm;         // p^{n-1}
+    const float* Kh;
+    float* out1;             // p^{n+1}
+    float* out2;             // p^{n+2}
+    const int32_t* ent_ptr;  // [2 ntiles + 1]: tile t has rows [2t, 2t+1) in the tile, [2t+1, 2t+2) in its ring
+    const int32_t* ent_code;
+    const float* ent_w;
+    PointSet<float> src;
+    const float* wavelet;
+    int step;                // n (the launch advances n -> n + 2)
+    PointSet<float> rec;
+    float* traces;
+    int nt;
+    int dw;
+    float da;
+};
+
+__device__ __forceinline__ void tb_decode(int32_t c, int& lx, int& lz, int& dx, int& dz) {
+    lx = c & 0xff;
+    lz = (c >> 8) & 0xff;
+    dx = (int)(int8_t)((c >> 16) & 0xff);
+    dz = (int)(int8_t)((c >> 24) & 0xff);
+}
+
+// dst[loc(e)] += w[e] * f[col(e)] for the entries [e0, e1): four chunks of 32
+// entries in flight per warp, segmented warp sums (entries of a row are
+// contiguous), one shared-memory atomic per row segment
+template <class LocCol>
+__device__ __forceinline__ void tb_entries(const TbArgs& a, int32_t e0, int32_t e1, LocCol lc, const float* f,
+                                           float* dst, int tid) {
+    constexpr int U = 4;
+    const int lane = tid & 31;
+    for (int32_t base = e0 + (tid & ~31) * U; base < e1; base += 256 * U) {
+        int32_t loc[U];
+        float val[U];
+        bool ok[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int32_t e = base + u * 32 + lane;
+            ok[u] = e < e1;
+            int l = -1 - lane, col = 0;
+            if (ok[u]) lc(a.ent_code[e], l, col);
+            loc[u] = l;
+            val[u] = ok[u] ? a.ent_w[e] * f[col] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) seg_add(dst, loc[u], val[u], ok[u], lane);
+    }
+}
+
+// dst[(z - zr) W + (x - xr)] += w wv for the source corners in the W x Z box at
+// (xr, zr) that are nodes of the model (corners in the zero padding are dropped,
+// as the one-step kernels drop them)
+__device__ __forceinline__ void tb_sources(const PointSet<float>& src, float wv, const Layout& L, int64_t xr,
+                                           int64_t zr, int W, int Z, float* dst, int tid) {
+    if (tid >= 8 * src.n) return;
+    const float w = src.w[tid];
+    if (w == 0.f) return;
+    const int64_t rel = src.idx[tid] - L.base;
+    const int64_t z = rel >= 0 ? rel / L.px : -((-rel + L.px - 1) / L.px);
+    const int64_t x = rel - z * L.px;
+    if (x >= L.nx || z < 0 || z >= L.nz) return;
+    const int64_t lx = x - xr, lz = z - zr;
+    if (lx >= 0 && lx < W && lz >= 0 && lz < Z) atomicAdd(&dst[lz * W + lx], w * wv);
+}
+
+template <int R, int TX, int TZ>
+struct TbShape {
+    static constexpr int W1 = TX + 2 * R, Z1 = TZ + 2 * R, W2 = TX + 4 * R, Z2 = TZ + 4 * R;
+    static constexpr size_t smem = sizeof(float) * ((size_t)W2 * Z2 + 2 * (size_t)W1 * Z1);
+    static_assert(W1 <= 256 && Z1 <= 256, "region-1 positions take 8 bits per axis");
+    static_assert((TX * TZ) % 256 == 0, "whole tile points per thread");
+};
+
+template <int H, int R, int TX, int TZ>
+__global__ void __launch_bounds__(256) k_leap2d_tb2(TbArgs a) {
+    using S = TbShape<R, TX, TZ>;
+    constexpr int W1 = S::W1, Z1 = S::Z1, W2 = S::W2, Z2 = S::Z2;
+    extern __shared__ float tb_sm[];
+    float* P0 = tb_sm;             // p^n on region 2
+    float* P1 = P0 + W2 * Z2;      // p^{n+1} on region 1
+    float* A = P1 + W1 * Z1;       // accumulator (region 1, then the tile)
+    const int tid = threadIdx.x;
+    const Layout& L = a.L;
+    const int64_t x0 = (int64_t)blockIdx.x * TX, z0 = (int64_t)blockIdx.y * TZ;
+    const int64_t tile = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+    // trace columns n - 1 (p^n) and n - 2 (p^{n-1}): both inputs of this launch
+    {
+        const int64_t gid = tile * 256 + tid, stride = launch_threads();
+        record_receivers(a.rec, a.pn, a.traces, a.nt, a.step - 1, gid, stride);
+        record_receivers(a.rec, a.pm, a.traces, a.nt, a.step - 2, gid, stride);
+    }
+    for (int i = tid; i < W2 * Z2; i += 256) {
+        const int lz = i / W2, lx = i - lz * W2;
+        const int64_t x = x0 + lx - 2 * R, z = z0 + lz - 2 * R;
+        const bool ok = x >= 0 && x < L.nx && z >= 0 && z < L.nz;
+        cp_async<4>(&P0[i], ok ? a.pn + L.base + z * L.px + x : a.pn, ok);
+    }
+    cp_async_commit();
+    const int32_t e0 = a.ent_ptr[2 * tile], em = a.ent_ptr[2 * tile + 1], e1 = a.ent_ptr[2 * tile + 2];
+    cp_async_wait_all();
+    __syncthreads();
+    // ---- step n -> n + 1 on region 1
+    for (int i = tid; i < W1 * Z1; i += 256) {
+        const int lz = i / W1, lx = i - lz * W1;
+        const float* q = P0 + (lz + R) * W2 + lx + R;
+        const float c = q[0];
+        float s = 0.f;
+#pragma unroll
+        for (int k = 1; k <= H; ++k)
+            s += a.w2[k] * (((q[k] - c) + (q[-k] - c)) + ((q[k * W2] - c) + (q[-k * W2] - c)));
+        A[i] = s;
+    }
+    __syncthreads();
+    if (e1 > e0)
+        tb_entries(
+            a, e0, e1,
+            [](int32_t code, int& loc, int& col) {
+                int lx, lz, dx, dz;
+                tb_decode(code, lx, lz, dx, dz);
+                loc = lz * W1 + lx;
+                col = (lz + R + dz) * W2 + lx + R + dx;
+            },
+            P0, A, tid);
+    __syncthreads();
+    // update (A keeps p^{n-1} for the absorbing layer), then the source
+    for (int i = tid; i < W1 * Z1; i += 256) {
+        const int lz = i / W1, lx = i - lz * W1;
+        const int64_t x = x0 + lx - R, z = z0 + lz - R;
+        float u = 0.f, pmv = 0.f;
+        if (x >= 0 && x < L.nx && z >= 0 && z < L.nz) {
+            const int64_t q = L.base + z * L.px + x;
+            const float c = P0[(lz + R) * W2 + lx + R];
+            pmv = a.pm[q];
+            u = c + ((c - pmv) + a.Kh[q] * A[i]);
+        }
+        P1[i] = u;
+        A[i] = pmv;
+    }
+    __syncthreads();
+    if (a.src.n) {
+        tb_sources(a.src, a.wavelet[a.step], L, x0 - R, z0 - R, W1, Z1, P1, tid);
+        __syncthreads();
+    }
+    if (damp_box(L, a.dw, x0 - R, x0 + TX - 1 + R, 0, 0, z0 + TZ - 1 + R)) {
+        for (int i = tid; i < W1 * Z1; i += 256) {
+            const int lz = i / W1, lx = i - lz * W1;
+            const int64_t x = x0 + lx - R, z = z0 + lz - R;
+            if (x >= 0 && x < L.nx && z >= 0 && z < L.nz)
+                P1[i] -= damp_g<float>(L, a.dw, a.da, x, 0, z) * (P1[i] - A[i]);
+        }
+    }
+    __syncthreads();
+    // ---- step n + 1 -> n + 2 on the tile
+    constexpr int PT = TX * TZ / 256;
+#pragma unroll
+    for (int j = 0; j < PT; ++j) {
+        const int i = tid + 256 * j, lz = i / TX, lx = i - lz * TX;
+        const float* q = P1 + (lz + R) * W1 + lx + R;
+        const float c = q[0];
+        float s = 0.f;
+#pragma unroll
+        for (int k = 1; k <= H; ++k)
+            s += a.w2[k] * (((q[k] - c) + (q[-k] - c)) + ((q[k * W1] - c) + (q[-k * W1] - c)));
+        A[i] = s;
+    }
+    __syncthreads();
+    if (em > e0)
+        tb_entries(
+            a, e0, em,
+            [](int32_t code, int& loc, int& col) {
+                int lx, lz, dx, dz;
+                tb_decode(code, lx, lz, dx, dz);
+                loc = (lz - R) * TX + lx - R;
+                col = (lz + dz) * W1 + lx + dx;
+            },
+            P1, A, tid);
+    __syncthreads();
+    float uv[PT];
+#pragma unroll
+    for (int j = 0; j < PT; ++j) {
+        const int i = tid + 256 * j, lz = i / TX, lx = i - lz * TX;
+        const int64_t x = x0 + lx, z = z0 + lz;
+        uv[j] = 0.f;
+        if (x < L.nx && z < L.nz) {
+            const int64_t q = L.base + z * L.px + x;
+            const float c = P1[(lz + R) * W1 + lx + R];
+            const float pmv = P0[(lz + 2 * R) * W2 + lx + 2 * R];
+            uv[j] = c + ((c - pmv) + a.Kh[q] * A[i]);
+            a.out1[q] = c;
+        }
+    }
+    if (a.src.n) {
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < PT; ++j) A[tid + 256 * j] = uv[j];
+        __syncthreads();
+        tb_sources(a.src, a.wavelet[a.step + 1], L, x0, z0, TX, TZ, A, tid);
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < PT; ++j) uv[j] = A[tid + 256 * j];
+    }
+    const bool damped = damp_box(L, a.dw, x0, x0 + TX - 1, 0, 0, z0 + TZ - 1);
+#pragma unroll
+    for (int j = 0; j < PT; ++j) {
+        const int i = tid + 256 * j, lz = i / TX, lx = i - lz * TX;
+        const int64_t x = x0 + lx, z = z0 + lz;
+        if (x >= L.nx || z >= L.nz) continue;
+        float u = uv[j];
+        if (damped) {
+            const float pmv = P0[(lz + 2 * R) * W2 + lx + 2 * R];
+            u -= damp_g<float>(L, a.dw, a.da, x, 0, z) * (u - pmv);
+        }
+        a.out2[L.base + z * L.px + x] = u;
+    }
+}
+
+static const int TBX = 64, TBZ = 32;
+
+// Correction entries of the two-step kernel for region margin R, cached in the
+// table's bins of operator 0 (key tx = TBX, ty = -R, tz = TBZ).  *ok = false
+// when a correction reaches further than R (the one-step kernels run then).
+static ib_status tb_bins(ib_table* t, int R, TileBins* out, bool* ok) {
+    IbOp& op = t->ops[0];
+    for (const TileBins& b : op.bins)
+        if (b.tx == TBX && b.ty == -R && b.tz == TBZ) {
+            *out = b;
+            *ok = b.nent >= 0;
+            return IB_OK;
+        }
+    const Layout& L = t->L;
+    const int64_t nr = op.nrows, nnz = op.nnz;
+    std::vector<int64_t> lin(nr), rp(nr + 1, 0);
+    std::vector<int32_t> code(nnz);
+    std::vector<float> w(nnz);
+    if (nr) {
+        IB_CUDA(cudaMemcpy(lin.data(), op.row_lin, 8 * nr, cudaMemcpyDeviceToHost));
+        IB_CUDA(cudaMemcpy(rp.data(), op.row_ptr, 8 * (nr + 1), cudaMemcpyDeviceToHost));
+    }
+    if (nnz) {
+        IB_CUDA(cudaMemcpy(code.data(), op.col_code, 4 * nnz, cudaMemcpyDeviceToHost));
+        IB_CUDA(cudaMemcpy(w.data(), op.w32, 4 * nnz, cudaMemcpyDeviceToHost));
+    }
+    TileBins b;
+    b.tx = TBX;
+    b.ty = -R;
+    b.tz = TBZ;
+    b.ntx = (L.nx + TBX - 1) / TBX;
+    b.nty = 1;
+    const int64_t ntz = (L.nz + TBZ - 1) / TBZ;
+    b.ntiles = b.ntx * ntz;
+    bool fits = true;
+    for (int64_t e = 0; e < nnz && fits; ++e) {
+        int dx, dy, dz;
+        unpack_off(code[e], dx, dy, dz);
+        fits = std::abs(dx) <= R && std::abs(dy) <= R;
+    }
+    if (!fits) {   // remembered, so that the check runs once per table
+        b.nent = -1;
+        op.bins.push_back(b);
+        *out = b;
+        *ok = false;
+        return IB_OK;
+    }
+    // visit (row, tile, in-tile?) for every tile whose region 1 holds the row
+    auto each = [&](auto&& f) {
+        for (int64_t r = 0; r < nr; ++r) {
+            const int64_t x = lin[r] % L.nx, z = lin[r] / L.nx;
+            for (int64_t bz = std::max<int64_t>(0, (z - R) / TBZ - 1); bz <= std::min(ntz - 1, (z + R) / TBZ); ++bz) {
+                if (z < bz * TBZ - R || z > bz * TBZ + TBZ - 1 + R) continue;
+                for (int64_t bx = std::max<int64_t>(0, (x - R) / TBX - 1); bx <= std::min(b.ntx - 1, (x + R) / TBX);
+                     ++bx) {
+                    if (x < bx * TBX - R || x > bx * TBX + TBX - 1 + R) continue;
+                    const bool in = x >= bx * TBX && x < bx * TBX + TBX && z >= bz * TBZ && z < bz * TBZ + TBZ;
+                    f(r, x, z, bx, bz, in);
+                }
+            }
+        }
+    };
+    std::vector<int64_t> cnt(2 * b.ntiles, 0);
+    each([&](int64_t r, int64_t, int64_t, int64_t bx, int64_t bz, bool in) {
+        cnt[2 * (bz * b.ntx + bx) + (in ? 0 : 1)] += rp[r + 1] - rp[r];
+    });
+    std::vector<int32_t> ptr(2 * b.ntiles + 1, 0);
+    int64_t tot = 0;
+    for (int64_t i = 0; i < 2 * b.ntiles; ++i) {
+        ptr[i] = (int32_t)tot;
+        tot += cnt[i];
+    }
+    if (tot >= INT32_MAX) {
+        ib_set_error("two-step correction list exceeds 2^31 entries");
+        return IB_ERR_ARG;
+    }
+    ptr[2 * b.ntiles] = (int32_t)tot;
+    std::vector<int32_t> ecode(std::max<int64_t>(tot, 1));
+    std::vector<float> ew(std::max<int64_t>(tot, 1));
+    std::vector<int64_t> cur(ptr.begin(), ptr.end() - 1);
+    each([&](int64_t r, int64_t x, int64_t z, int64_t bx, int64_t bz, bool in) {
+        const uint32_t lx = (uint32_t)(x - (bx * TBX - R)), lz = (uint32_t)(z - (bz * TBZ - R));
+        int64_t& c = cur[2 * (bz * b.ntx + bx) + (in ? 0 : 1)];
+        for (int64_t e = rp[r]; e < rp[r + 1]; ++e, ++c) {
+            int dx, dy, dz;
+            unpack_off(code[e], dx, dy, dz);
+            ecode[c] = (int32_t)(lx | lz << 8 | (uint32_t)(dx & 0xff) << 16 | (uint32_t)(dy & 0xff) << 24);
+            ew[c] = w[e];
+        }
+    });
+    b.nent = tot;
+    auto up = [](auto** d, const auto& v) -> ib_status {
+        IB_CUDA(cudaMalloc((void**)d, sizeof(v[0]) * v.size()));
+        IB_CUDA(cudaMemcpy(*d, v.data(), sizeof(v[0]) * v.size(), cudaMemcpyHostToDevice));
+        return IB_OK;
+    };
+    ib_status st = up(&b.ent_ptr, ptr);
+    if (st == IB_OK) st = up(&b.ent_loc, ecode);
+    if (st == IB_OK) st = up(&b.ent_w32, ew);
+    if (st != IB_OK) {
+        ib_free_bins(b);
+        return st;
+    }
+    op.bins.push_back(b);
+    *out = b;
+    *ok = true;
+    return IB_OK;
+}
+
+// IB_TEMPORAL_BLOCK=0 / 1 turns the two-step kernel off / on
+static bool tb_enabled() {
+    const char* e = getenv("IB_TEMPORAL_BLOCK");
+    return e && e[0] == '1';
+}
+
+template <int H, int R>
+static void launch_tb2_hr(const TbArgs& a, dim3 grid, cudaStream_t s) {
+    using Sh = TbShape<R, TBX, TBZ>;
+    static const bool attr = (cudaFuncSetAttribute(k_leap2d_tb2<H, R, TBX, TBZ>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Sh::smem),
+                              true);
+    (void)attr;
+    k_leap2d_tb2<H, R, TBX, TBZ><<<grid, 256, Sh::smem, s>>>(a);
+}
+template <int R>
+static void launch_tb2_r(const TbArgs& a, int H, dim3 grid, cudaStream_t s) {
+    if (H == 1) launch_tb2_hr<1, R>(a, grid, s);
+    else if (H == 2) launch_tb2_hr<2, R>(a, grid, s);
+    else if (H == 3) launch_tb2_hr<3, R>(a, grid, s);
+    else launch_tb2_hr<4, R>(a, grid, s);
+}
+// region margins the two-step kernel is built for (R >= M/2 and >= the reach)
+static const int TB_MARGINS[2] = {4, 6};
+static void launch_tb2(const TbArgs& a, int H, int R, dim3 grid, cudaStream_t s) {
+    PROF_LAUNCH("leap2d_tb2_f32", s, {
+        if (R == 4) launch_tb2_r<4>(a, H, grid, s);
+        else launch_tb2_r<6>(a, H, grid, s);
+    });
+}
+
 template <typename T>
 static ib_status forward_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, void* ckpt, int n_ckpt,
                              cudaStream_t s, const Probe* probe = nullptr) {
@@ -2036,6 +2661,25 @@ static ib_status forward_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, 
     T* prev = p1;  // p^{n-1}
     dim3 grid2((unsigned)((L.nx + TX2 - 1) / TX2), (unsigned)((L.nz + TZ2 - 1) / TZ2));
     const bool strips = d == 2 && sizeof(T) == 4 && use_strips(L);
+    // two steps per launch (FP32 2D; not with checkpoints or the stability probe)
+    int tbR = 0;
+    TileBins tbb;
+    float *tb_o1 = nullptr, *tb_o2 = nullptr;
+    if (d == 2 && sizeof(T) == 4 && !ckpt && !probe && nt >= 2 && tb_enabled()) {
+        for (int R : TB_MARGINS) {
+            if (R < H) continue;
+            bool ok = false;
+            TRY(tb_bins(t, R, &tbb, &ok));
+            if (ok) {
+                tbR = R;
+                break;
+            }
+        }
+        if (tbR) {
+            TRY(S.alloc(&tb_o1, L.total, true));
+            TRY(S.alloc(&tb_o2, L.total, true));
+        }
+    }
     dim3 grids((unsigned)((L.nx + TX2 - 1) / TX2),
                (unsigned)(((L.nz + TZ2 - 1) / TZ2 + STRIP_NSUB - 1) / STRIP_NSUB));
     // planes per 3D block (IB_ZCHUNK overrides it for tuning)
@@ -2051,15 +2695,24 @@ static ib_status forward_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, 
     const uint16_t* code16 = nullptr;
     int* err = nullptr;
     const bool use_tma = d == 3 && sizeof(T) == 4 && tma_enabled();
+    // x-pair kernel (64 x 8 tiles; IB_TMA3_PAIRS=0 selects the 32 x 8 kernel)
+    bool pairs = false;
+    // correction pass: entries in flight per lane, 4 (IB_ADD3_U=8 selects 8: at
+    // 512^2 x 384, order 8, 150 us per launch against 141 us with 4)
+    int add3_u = 4;
+    if (const char* e = getenv("IB_ADD3_U")) add3_u = atoi(e) == 8 ? 8 : 4;
     if (use_tma) {
-        TRY(make_plane_map(tmap[0], (void*)p0, L));
-        TRY(make_plane_map(tmap[1], (void*)p1, L));
-        TRY(make_plane_map(tmtile[0], (void*)p0, L, true));
-        TRY(make_plane_map(tmtile[1], (void*)p1, L, true));
-        TRY(make_plane_map(tmK, (void*)Kh, L, true));
+        const char* fe = getenv("IB_FUSED3");
+        const char* pe = getenv("IB_TMA3_PAIRS");
+        pairs = !(fe && fe[0] == '1') && !(pe && pe[0] == '0');
+        const uint32_t tw = pairs ? 64 : 32;
+        TRY(make_plane_map(tmap[0], (void*)p0, L, false, tw));
+        TRY(make_plane_map(tmap[1], (void*)p1, L, false, tw));
+        TRY(make_plane_map(tmtile[0], (void*)p0, L, true, tw));
+        TRY(make_plane_map(tmtile[1], (void*)p1, L, true, tw));
+        TRY(make_plane_map(tmK, (void*)Kh, L, true, tw));
         TRY(S.alloc(&err, 1, true));
         // corrections: fused into the step kernel (IB_FUSED3=1) or added by k_ib_add3
-        const char* fe = getenv("IB_FUSED3");
         if (fe && fe[0] == '1') {
             if (bins && bins->nent > 0) {
                 rows3.ptr = bins->ent_ptr;
@@ -2071,7 +2724,48 @@ static ib_status forward_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, 
             TRY(ib_table_code16(t, 0, &code16, s));
         }
     }
-    for (int n = 0; n < nt; ++n) {
+    int n0 = 0;
+    if (tbR) {
+        TbArgs ta;
+        memset(&ta, 0, sizeof ta);
+        ta.L = L;
+        for (int k = 0; k < 5; ++k) ta.w2[k] = (float)a.w2[k];
+        ta.Kh = (const float*)Kh;
+        ta.ent_ptr = tbb.ent_ptr;
+        ta.ent_code = tbb.ent_loc;
+        ta.ent_w = tbb.ent_w32;
+        ta.src = *reinterpret_cast<const PointSet<float>*>(&g.src);
+        ta.wavelet = (const float*)sh->wavelet_dev;
+        ta.rec = *reinterpret_cast<const PointSet<float>*>(&g.rec);
+        ta.traces = (float*)sh->traces_dev;
+        ta.nt = nt;
+        ta.dw = a.dw;
+        ta.da = (float)a.da;
+        dim3 gtb((unsigned)((L.nx + TBX - 1) / TBX), (unsigned)((L.nz + TBZ - 1) / TBZ));
+        float *pc = (float*)cur, *pp = (float*)prev;
+        for (; n0 + 2 <= nt; n0 += 2) {
+            ta.pn = pc;
+            ta.pm = pp;
+            ta.out1 = tb_o1;
+            ta.out2 = tb_o2;
+            ta.step = n0;
+            launch_tb2(ta, H, tbR, gtb, s);
+            IB_CHECK_LAUNCH("two-step leapfrog");
+            // p^{n+1}, p^{n+2} become (prev, cur); the old pair takes the next outputs
+            tb_o1 = pp;
+            tb_o2 = pc;
+            pp = ta.out1;
+            pc = ta.out2;
+        }
+        cur = (T*)pc;
+        prev = (T*)pp;
+        if (g.rec.n) {   // trace column n - 2 (p^{n-1}): the launches recorded columns up to n - 3
+            k_receivers<T><<<grid1(g.rec.n, 256), 256, 0, s>>>(g.rec, prev, (T*)sh->traces_dev, nt, n0 - 2);
+            IB_CHECK_LAUNCH("k_receivers");
+            ib_count_launch("setup");
+        }
+    }
+    for (int n = n0; n < nt; ++n) {
         if (ckpt && n % seg == 0) {
             T* slot = (T*)ckpt + (int64_t)(n / seg) * 2 * L.total;
             IB_CUDA(cudaMemcpyAsync(slot, cur, sizeof(T) * L.total, cudaMemcpyDeviceToDevice, s));
@@ -2092,7 +2786,13 @@ static ib_status forward_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, 
             const CUtensorMap& tmm = (cur == p0) ? tmtile[1] : tmtile[0];   // p_prev: the other buffer
             PROF_LAUNCH("leap3d_tma_f32", s, {
                 const StepArgs<float>& af = *reinterpret_cast<const StepArgs<float>*>(&a);
-                if (H == 1) launch_leap3d_tma<1>(af, tmc, tmm, tmK, rows3, zchunk, nty3, err, grid3, s);
+                if (pairs) {
+                    dim3 gp((unsigned)((L.nx + 63) / 64), grid3.y, grid3.z);
+                    if (H == 1) launch_leap3d_tma2<1>(af, tmc, tmm, tmK, zchunk, err, gp, s);
+                    else if (H == 2) launch_leap3d_tma2<2>(af, tmc, tmm, tmK, zchunk, err, gp, s);
+                    else if (H == 3) launch_leap3d_tma2<3>(af, tmc, tmm, tmK, zchunk, err, gp, s);
+                    else launch_leap3d_tma2<4>(af, tmc, tmm, tmK, zchunk, err, gp, s);
+                } else if (H == 1) launch_leap3d_tma<1>(af, tmc, tmm, tmK, rows3, zchunk, nty3, err, grid3, s);
                 else if (H == 2) launch_leap3d_tma<2>(af, tmc, tmm, tmK, rows3, zchunk, nty3, err, grid3, s);
                 else if (H == 3) launch_leap3d_tma<3>(af, tmc, tmm, tmK, rows3, zchunk, nty3, err, grid3, s);
                 else launch_leap3d_tma<4>(af, tmc, tmm, tmK, rows3, zchunk, nty3, err, grid3, s);
@@ -2100,9 +2800,14 @@ static ib_status forward_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, 
             if (code16) {
                 const IbOp& op = t->ops[0];
                 PROF_LAUNCH("ib_add3_f32", s, {
-                    k_ib_add3<<<grid1(op.nrows * 32, 256), 256, 0, s>>>(
-                        op.nrows, op.row_pad, op.row_ptr, code16, op.w32, (const float*)a.p, (const float*)Kh,
-                        (float*)a.out, L, a.dw, (float)a.da);
+                    if (add3_u == 4)
+                        k_ib_add3<4><<<grid1(op.nrows * 32, 256), 256, 0, s>>>(
+                            op.nrows, op.row_pad, op.row_ptr, code16, op.w32, (const float*)a.p, (const float*)Kh,
+                            (float*)a.out, L, a.dw, (float)a.da);
+                    else
+                        k_ib_add3<8><<<grid1(op.nrows * 32, 256), 256, 0, s>>>(
+                            op.nrows, op.row_pad, op.row_ptr, code16, op.w32, (const float*)a.p, (const float*)Kh,
+                            (float*)a.out, L, a.dw, (float)a.da);
                 });
             }
         } else {

@@ -429,6 +429,63 @@ def test_forward_3d_tma_matches_plain_loads(monkeypatch):
     assert rel_l2(tma, plain) < 1e-6
 
 
+@pytest.mark.parametrize("damped", [False, True])
+def test_forward_3d_pairs_match_single_points(damped, monkeypatch):
+    """The default FP32 3D kernel computes two x-adjacent points per thread on
+    64 x 8 tiles; IB_TMA3_PAIRS=0 selects the kernel with one point per thread
+    on 32 x 8 tiles.  Same traces on a grid of 2 ragged x tiles (nx = 70) with
+    the source spread over the corner of four tiles, with and without the
+    absorbing layer."""
+    sdf, zs = small_hills(nx=70, ny=20, nz=30)
+    h = 10.0
+    vel = np.full(sdf.shape, 1800.0)
+    dt = 0.4 * h / 1800.0
+    nt = 100
+    src = np.array([[63.6 * h, 7.5 * h, 20.2 * h]])
+    rec = np.array([[x * h, y * h, zs[y, x] + 2 * h] for x in range(2, 68, 5) for y in range(2, 18, 5)])
+    rec = np.concatenate([src, rec])
+    w = dict(sdf=sdf, vel=vel, h=h, M=8, dt=dt, nt=nt, src=src, rec=rec, wavelet=inputs.ricker(25.0, dt, nt))
+    damp = (5, 1.5 * 1800.0 / (5 * h) * math.log(1e6)) if damped else None
+    t = ib.ib_build_stencils(cuda(sdf), h, "free", "second", 8)
+    out = {}
+    for mode in ("1", "0"):
+        monkeypatch.setenv("IB_TMA3_PAIRS", mode)
+        tr = ib.ib_forward(t, cuda(vel, torch.float32), cuda(w["wavelet"], torch.float32), cuda(src), cuda(rec),
+                           dt, nt, damp=damp)
+        ib.ib_sync_status()
+        out[mode] = tr.double().cpu().numpy()
+    assert np.abs(out["0"]).max() > 0
+    assert rel_l2(out["1"], out["0"]) < 1e-6
+    if not damped:
+        ref = _oracle_leap(w, "free")
+        e = rel_l2(out["1"], ref)
+        record("pairs3d_70x20x30", e32=e)
+        assert e < TOL32, e
+
+
+def test_forward_3d_correction_pass_rounds(monkeypatch):
+    """The 3D correction pass takes each lane's entries 4 at a time by default
+    and 8 at a time with IB_ADD3_U=8: the same entries in the same order per
+    lane, so the traces are identical bit for bit."""
+    sdf, zs = small_hills()
+    h = 10.0
+    vel = np.full(sdf.shape, 1800.0)
+    dt = 0.4 * h / 1800.0
+    nt = 60
+    src = np.array([[20 * h, 17 * h, 26 * h]])
+    rec = np.array([[x * h, y * h, zs[y, x] + 2 * h] for x in range(4, 36, 5) for y in range(4, 32, 5)])
+    t = ib.ib_build_stencils(cuda(sdf), h, "free", "second", 8)
+    out = {}
+    for u in ("8", "4"):
+        monkeypatch.setenv("IB_ADD3_U", u)
+        tr = ib.ib_forward(t, cuda(vel, torch.float32), cuda(inputs.ricker(25.0, dt, nt), torch.float32), cuda(src),
+                           cuda(rec), dt, nt)
+        ib.ib_sync_status()
+        out[u] = tr.cpu().numpy()
+    assert np.abs(out["4"]).max() > 0
+    assert np.array_equal(out["8"], out["4"])
+
+
 # ---------------------------------------------------------------------------
 # FP32 adjoint against the oracle, and the gradient against finite differences
 # ---------------------------------------------------------------------------
