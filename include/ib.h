@@ -242,7 +242,7 @@ ib_status ib_adjoint(const ib_table* table, const ib_shot* shot, int32_t precisi
  * and topography), advanced together: every time step is one launch that
  * covers the tiles (or z-marched strips of tiles) of all shots, and all steps
  * are one captured CUDA graph.  The tile shape is timed on the first batch of
- * a size class and remembered; the environment variable IB_BATCH_SHAPE=<0..7>
+ * a size class and remembered; the environment variable IB_BATCH_SHAPE=<0..9>
  * fixes it instead (IB_ERR_ARG outside that range).  Same semantics per shot
  * as ib_forward (precision 32, no checkpoints).  tables[i] and shots[i] are
  * host arrays of length nshot.

@@ -562,6 +562,207 @@ __global__ void __launch_bounds__(256, 4) k_leap2d_m(StepArgs<float> a) {
     leap2d_strip<H, NSUB, D>(a, blockIdx.x, blockIdx.y, sm);
 }
 
+// ---------------------------------------------------------------------------
+// Strips of 64 x 16 tiles with four points per thread (two x-adjacent columns
+// of two rows): the z-marched strip of leap2d_strip with the x-pair layout of
+// the 3D step.  Per tile a thread loads its two columns' 2H + 2 rows as 8-byte
+// pairs and each of its rows' x neighbours (-4 .. +5) in five 8-byte loads, and
+// the copy issue, waits, barriers and epilogue serve four points.  The strip is
+// NSUB tiles deep and held whole in shared memory; D tiles are in flight.  The
+// arithmetic per point is that of leap2d_tile.
+// ---------------------------------------------------------------------------
+template <int H, int NSUB, int D>
+struct Strip4 {
+    static constexpr int TX = 64, TZ = 16, W = TX + 8, CH = W / 4, ROWS = NSUB * TZ + 2 * H;
+    static constexpr int STAGE = TZ * TX;
+    // floats: rows, p_prev and K stages, acc, sadd
+    static constexpr size_t FLOATS = (size_t)ROWS * W + 2 * (D + 1) * STAGE + 2 * STAGE;
+    static_assert(H <= 4 && 2 * H <= TZ, "x halo of 4 and one tile of look-ahead rows");
+};
+
+template <int H, int NSUB, int D>
+__device__ __forceinline__ void leap2d_strip4(const StepArgs<float>& a, int64_t bx, int64_t bzc, float* smem) {
+    using S = Strip4<H, NSUB, D>;
+    constexpr int TX = S::TX, TZ = S::TZ, W = S::W, CH = S::CH, STAGE = S::STAGE;
+    float* rows = smem;                                  // [ROWS][W], row j <-> z = zs - H + j
+    float* pm = rows + S::ROWS * W;                      // [D + 1][STAGE]
+    float* kh = pm + (D + 1) * STAGE;                    // [D + 1][STAGE]
+    float* acc = kh + (D + 1) * STAGE;                   // [STAGE]
+    float* sadd = acc + STAGE;                           // [STAGE]
+    const int tid = threadIdx.x;
+    const Layout& L = a.L;
+    const int64_t ntz = (L.nz + TZ - 1) / TZ;
+    const int64_t bz0 = bzc * NSUB;
+    const int nsub = (int)(ntz - bz0 < NSUB ? ntz - bz0 : NSUB);
+    const int64_t x0 = bx * TX, zs = bz0 * TZ;
+    const int64_t qlim = L.total - 4;
+    // copies of tile t: its new rows of p (all TZ + 2H rows for t = 0), and its
+    // p_prev and K (chunk tid of each: row tid >> 4, columns 4 (tid & 15) ..)
+    auto issue = [&](int t) {
+        if (t < nsub) {
+            const int j0 = t == 0 ? 0 : t * TZ + 2 * H;           // first strip row to fetch
+            const int nr = t == 0 ? TZ + 2 * H : TZ;
+            for (int c = tid; c < nr * CH; c += 256) {
+                const int r = c / CH, pc = c - r * CH;
+                const int j = j0 + r;
+                const int64_t z = zs - H + j;
+                const int64_t q = (z + H + 1) * L.px + x0 - 4 + 4 * pc;
+                const bool ok = z < L.nz + H && q <= qlim;
+                cp_async16(smem_u32(rows + j * W + 4 * pc), ok ? a.p + q : a.p, ok);
+            }
+            const int st = t % (D + 1);
+            const int qr = tid >> 4, qc = tid & 15;
+            const int64_t z = zs + (int64_t)t * TZ + qr;
+            const int64_t q = (z + H + 1) * L.px + x0 + 4 * qc;
+            const bool ok = z < L.nz && q <= qlim;
+            cp_async16(smem_u32(pm + st * STAGE + qr * TX + 4 * qc), ok ? a.pm + q : a.pm, ok);
+            cp_async16(smem_u32(kh + st * STAGE + qr * TX + 4 * qc), ok ? a.Kh + q : a.Kh, ok);
+        }
+        cp_async_commit();   // empty groups keep the count uniform
+    };
+    const int cx = tid & 31, rz = tid >> 5;
+    const int lx = 2 * cx, lz0 = 2 * rz;                // points (lz0 + j, lx + k), j, k in {0, 1}
+    const int i0 = lz0 * TX + lx;
+    *reinterpret_cast<float2*>(sadd + i0) = make_float2(0.f, 0.f);
+    *reinterpret_cast<float2*>(sadd + i0 + TX) = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int t = 0; t < D; ++t) issue(t);
+    int srow = -1, scol = 0;
+    float sw = 0.f;
+    const float wv = a.src.n ? a.wavelet[a.step] : 0.f;
+    if (tid < 8 * a.src.n) {
+        const int64_t rel = a.src.idx[tid] - (L.base + zs * L.px + x0);
+        if (rel >= 0) {
+            const int64_t r = rel / L.px, c = rel - r * L.px;
+            if (r < NSUB * TZ && c < TX && a.src.w[tid] != 0.f) {
+                srow = (int)r;
+                scol = (int)c;
+                sw = a.src.w[tid] * wv;
+            }
+        }
+    }
+    const int32_t* pp = a.op.ptr ? a.op.ptr + bz0 * a.op.ntx + bx : nullptr;
+    int32_t e0 = 0, e1 = 0;
+    if (pp) {
+        e0 = pp[0];
+        e1 = pp[1];
+    }
+    const float* colp = rows + lz0 * W + lx + 4;        // this thread's column pair, tile s
+    const bool xa = x0 + lx < L.nx, xb = x0 + lx + 1 < L.nx;
+    const int zleft = (int)(L.nz - zs) - lz0;           // rows of this thread left to store
+    float* outp = a.out + (zs + lz0 + H + 1) * L.px + x0 + lx;
+    int64_t origin = L.base + zs * L.px + x0;
+#pragma unroll 1
+    for (int s = 0; s < nsub; ++s) {
+        cp_async_wait_group<D - 1>();
+        __syncthreads();   // tile s has landed; tile s - 1 is done with its buffers
+        issue(s + D);
+        int32_t f0 = 0, f1 = 0;
+        if (s + 1 < nsub && pp) {
+            pp += a.op.ntx;
+            f0 = pp[0];
+            f1 = pp[1];
+        }
+        float2 v[2 * H + 2];   // rows lz0 - H .. lz0 + 1 + H of the two columns
+#pragma unroll
+        for (int m = 0; m < 2 * H + 2; ++m) v[m] = *reinterpret_cast<const float2*>(colp + m * W);
+        float2 cv[2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const float* r0 = colp + (H + j) * W;
+            float2 xr[5];   // r0[-4 .. 5]
+#pragma unroll
+            for (int i = 0; i < 5; ++i) xr[i] = *reinterpret_cast<const float2*>(r0 + 2 * i - 4);
+            auto X = [&](int o) -> float {
+                const int i = o + 4;
+                return (i & 1) ? xr[i >> 1].y : xr[i >> 1].x;
+            };
+            const float ca = v[H + j].x, cb = v[H + j].y;
+            float sa = 0.f, sb = 0.f;
+#pragma unroll
+            for (int k = 1; k <= H; ++k) {
+                sa += a.w2[k] * (((X(k) - ca) + (X(-k) - ca)) + ((v[H + j + k].x - ca) + (v[H + j - k].x - ca)));
+                sb += a.w2[k] * (((X(1 + k) - cb) + (X(1 - k) - cb)) + ((v[H + j + k].y - cb) + (v[H + j - k].y - cb)));
+            }
+            *reinterpret_cast<float2*>(acc + i0 + j * TX) = make_float2(sa, sb);
+            cv[j] = make_float2(ca, cb);
+        }
+        {
+            const int ly = srow - s * TZ;
+            if (srow >= 0 && ly >= 0 && ly < TZ) atomicAdd(&sadd[ly * TX + scol], sw);
+        }
+        __syncthreads();
+        if (e1 > e0) {
+            add_entries_range(a.op, e0, e1, a.p, origin, acc, tid, 256);
+            __syncthreads();
+        }
+        const int st = s % (D + 1);
+        const float* pmS = pm + st * STAGE;
+        const float* khS = kh + st * STAGE;
+        const bool damped = damp_box(L, a.dw, x0, x0 + TX - 1, 0, 0, zs + (s + 1) * TZ - 1);
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const int i = i0 + j * TX;
+            const float2 pmv = *reinterpret_cast<const float2*>(pmS + i);
+            const float2 khv = *reinterpret_cast<const float2*>(khS + i);
+            const float2 ac = *reinterpret_cast<const float2*>(acc + i);
+            const float2 sd = *reinterpret_cast<const float2*>(sadd + i);
+            const float c0 = cv[j].x, c1 = cv[j].y;
+            float u0 = c0 + ((c0 - pmv.x) + khv.x * ac.x) + sd.x;
+            float u1 = c1 + ((c1 - pmv.y) + khv.y * ac.y) + sd.y;
+            if (damped) {
+                const int64_t z = zs + s * TZ + lz0 + j;
+                u0 -= damp_g<float>(L, a.dw, a.da, x0 + lx, 0, z) * (u0 - pmv.x);
+                u1 -= damp_g<float>(L, a.dw, a.da, x0 + lx + 1, 0, z) * (u1 - pmv.y);
+            }
+            if (s * TZ + j < zleft) {
+                if (xb) *reinterpret_cast<float2*>(outp + j * L.px) = make_float2(u0, u1);
+                else if (xa) outp[j * L.px] = u0;
+            }
+            *reinterpret_cast<float2*>(sadd + i) = make_float2(0.f, 0.f);
+        }
+        e0 = f0;
+        e1 = f1;
+        colp += TZ * W;
+        outp += TZ * L.px;
+        origin += TZ * L.px;
+    }
+    cp_async_wait_group<0>();   // the empty groups past the strip's end
+}
+
+// many shots in one launch, each block a z-marched strip of 64 x 16 tiles
+template <int H, int NSUB, int D, int MINB>
+__global__ void __launch_bounds__(256, MINB) k_leap2d_batch_m4(const StepArgs<float>* __restrict__ shots,
+                                                               const int64_t* __restrict__ tile0,
+                                                               const int32_t* __restrict__ shot_of, int nshot,
+                                                               int step) {
+    extern __shared__ __align__(16) float strip4_sm[];
+    const int64_t b = blockIdx.x;
+    const int lo = shot_of[b];
+    StepArgs<float> a = shots[lo];
+    const int64_t local = b - tile0[lo];
+    float* cur = (step & 1) ? a.buf1 : a.buf0;
+    float* prev = (step & 1) ? a.buf0 : a.buf1;
+    a.p = cur;
+    a.pm = prev;
+    a.out = prev;
+    a.step = step;
+    a.rec_step = step - 1;
+    record_receivers(a.rec, a.p, a.traces, a.nt, a.rec_step, local * 256 + threadIdx.x,
+                     (tile0[lo + 1] - tile0[lo]) * 256);
+    if (local >= a.ntiles) return;   // uniform per block
+    leap2d_strip4<H, NSUB, D>(a, local % a.ntx, local / a.ntx, strip4_sm);
+}
+
+// one shot, FP32: block (x, y) is the z-marched strip of column x and chunk y
+template <int H, int NSUB, int D>
+__global__ void __launch_bounds__(256, 3) k_leap2d_m4(StepArgs<float> a) {
+    extern __shared__ __align__(16) float strip4_sm[];
+    const int64_t blk = (int64_t)blockIdx.y * gridDim.x + blockIdx.x;
+    record_receivers(a.rec, a.p, a.traces, a.nt, a.rec_step, blk * 256 + threadIdx.x, launch_threads());
+    leap2d_strip4<H, NSUB, D>(a, blockIdx.x, blockIdx.y, strip4_sm);
+}
+
 // Batched recompute step n of a checkpoint segment, on z-marched strips: the
 // shot's segment buffer (buf0) holds p^{c-1+j} in slot j, and step n = c + j
 // writes slot j + 2.  The block map counts strips, ntx * ceil(ceil(nz / 8) / NSUB)
@@ -2616,6 +2817,32 @@ static void launch_tb2(const TbArgs& a, int H, int R, dim3 grid, cudaStream_t s)
     });
 }
 
+// Single FP32 shots on strips use 64 x 16 tiles with two columns per thread
+// (IB_STRIP4=0 selects the 64 x 8 strips): 134 against 176 us per step at
+// 8192 x 4096, order 8.
+static bool strip4_enabled() {
+    const char* e = getenv("IB_STRIP4");
+    return !(e && e[0] == '0');
+}
+
+template <int H>
+static void launch_strip4_h(const StepArgs<float>& a, dim3 grid, cudaStream_t s) {
+    constexpr size_t sm = Strip4<H, 4, 2>::FLOATS * sizeof(float);
+    static const bool attr = (cudaFuncSetAttribute(k_leap2d_m4<H, 4, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   (int)sm),
+                              true);
+    (void)attr;
+    k_leap2d_m4<H, 4, 2><<<grid, 256, sm, s>>>(a);
+}
+static void launch_leap2d_strip4(const StepArgs<float>& a, int H, dim3 grid, cudaStream_t s) {
+    PROF_LAUNCH("leap2d_strip_f32", s, {
+        if (H == 1) launch_strip4_h<1>(a, grid, s);
+        else if (H == 2) launch_strip4_h<2>(a, grid, s);
+        else if (H == 3) launch_strip4_h<3>(a, grid, s);
+        else launch_strip4_h<4>(a, grid, s);
+    });
+}
+
 template <typename T>
 static ib_status forward_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, void* ckpt, int n_ckpt,
                              cudaStream_t s, const Probe* probe = nullptr) {
@@ -2661,6 +2888,15 @@ static ib_status forward_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, 
     T* prev = p1;  // p^{n-1}
     dim3 grid2((unsigned)((L.nx + TX2 - 1) / TX2), (unsigned)((L.nz + TZ2 - 1) / TZ2));
     const bool strips = d == 2 && sizeof(T) == 4 && use_strips(L);
+    // strips of 64 x 16 tiles, two columns per thread (default; IB_STRIP4=0: 64 x 8)
+    const bool strip4 = strips && strip4_enabled();
+    StepArgs<T> a4 = a;
+    dim3 grid4((unsigned)((L.nx + 63) / 64), (unsigned)(((L.nz + 15) / 16 + 3) / 4));
+    if (strip4) {
+        const TileBins* b4 = nullptr;
+        TRY(ib_table_bins(t, 0, false, 64, 1, 16, &b4, s));
+        a4.op = tview<T>(b4);
+    }
     // two steps per launch (FP32 2D; not with checkpoints or the stability probe)
     int tbR = 0;
     TileBins tbb;
@@ -2776,7 +3012,14 @@ static ib_status forward_2nd(ib_table* t, const ib_shot* sh, double dt, int nt, 
         a.out = prev;
         a.step = n;
         a.rec_step = n - 1;
-        if (strips) {
+        if (strip4) {
+            a4.p = a.p;
+            a4.pm = a.pm;
+            a4.out = a.out;
+            a4.step = a.step;
+            a4.rec_step = a.rec_step;
+            launch_leap2d_strip4(*reinterpret_cast<const StepArgs<float>*>(&a4), H, grid4, s);
+        } else if (strips) {
             launch_leap2d_strip(*reinterpret_cast<const StepArgs<float>*>(&a), H, grids, s);
         } else if (d == 2) {
             launch_leap2d<T>(a, H, grid2, s);
@@ -3639,9 +3882,10 @@ extern "C" ib_status ib_adjoint(const ib_table* tc, const ib_shot* sh, int32_t p
 struct TileShape {
     int tx, tz, nsub;   // nsub > 1: z-marched strips of nsub tiles (k_leap2d_batch_m)
 };
-static const int kNumShapes = 8;
-static const TileShape kShapes[kNumShapes] = {{64, 8, 1}, {32, 16, 1}, {128, 4, 1}, {64, 4, 1},
-                                              {64, 8, 8}, {64, 8, 8}, {64, 8, 8}, {64, 8, 8}};
+static const int kNumShapes = 10;
+static const TileShape kShapes[kNumShapes] = {{64, 8, 1},  {32, 16, 1}, {128, 4, 1}, {64, 4, 1},
+                                              {64, 8, 8},  {64, 8, 8},  {64, 8, 8},  {64, 8, 8},
+                                              {64, 16, 4}, {64, 16, 4}};
 
 template <int H, int TX, int TZ>
 static void launch_batch(const StepArgs<float>* args, const int64_t* tile0, const int32_t* shot_of, int nshot,
@@ -3656,6 +3900,17 @@ static void launch_batch_m(const StepArgs<float>* args, const int64_t* tile0, co
     k_leap2d_batch_m<H, NSUB, D, MINB><<<(unsigned)nblk, 256, 0, s>>>(args, tile0, shot_of, nshot, step);
 }
 
+template <int H, int NSUB, int D, int MINB>
+static void launch_batch_m4(const StepArgs<float>* args, const int64_t* tile0, const int32_t* shot_of, int nshot,
+                            int step, int64_t nblk, cudaStream_t s) {
+    constexpr size_t sm = Strip4<H, NSUB, D>::FLOATS * sizeof(float);
+    static const bool attr = (cudaFuncSetAttribute(k_leap2d_batch_m4<H, NSUB, D, MINB>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm),
+                              true);
+    (void)attr;
+    k_leap2d_batch_m4<H, NSUB, D, MINB><<<(unsigned)nblk, 256, sm, s>>>(args, tile0, shot_of, nshot, step);
+}
+
 template <int H>
 static void launch_batch_shape(int si, const StepArgs<float>* args, const int64_t* tile0, const int32_t* shot_of,
                                int nshot, int step,
@@ -3668,7 +3923,9 @@ static void launch_batch_shape(int si, const StepArgs<float>* args, const int64_
         case 4: launch_batch_m<H, 8, 2, 4>(args, tile0, shot_of, nshot, step, nblk, s); break;
         case 5: launch_batch_m<H, 8, 3, 4>(args, tile0, shot_of, nshot, step, nblk, s); break;
         case 6: launch_batch_m<H, 8, 2, 5>(args, tile0, shot_of, nshot, step, nblk, s); break;
-        default: launch_batch_m<H, 8, 3, 5>(args, tile0, shot_of, nshot, step, nblk, s); break;
+        case 7: launch_batch_m<H, 8, 3, 5>(args, tile0, shot_of, nshot, step, nblk, s); break;
+        case 8: launch_batch_m4<H, 4, 2, 3>(args, tile0, shot_of, nshot, step, nblk, s); break;
+        default: launch_batch_m4<H, 4, 3, 3>(args, tile0, shot_of, nshot, step, nblk, s); break;
     }
 }
 
@@ -3800,7 +4057,7 @@ static ib_status forward_batch_impl(const ib_table* const* tables, const ib_shot
     if (forced && *forced) {
         best = atoi(forced);
         if (best < 0 || best >= kNumShapes) {
-            ib_set_error("IB_BATCH_SHAPE must name a tile shape index in [0, 8)");
+            ib_set_error("IB_BATCH_SHAPE must name a tile shape index in [0, 10)");
             return IB_ERR_ARG;
         }
     } else {

@@ -334,11 +334,12 @@ def test_forward_batch_matches_single_shots():
     assert rel_l2(outs[0].double().cpu().numpy(), ref) < TOL32
 
 
-@pytest.mark.parametrize("shape", range(8))
+@pytest.mark.parametrize("shape", range(10))
 def test_forward_batch_every_tile_shape(shape, monkeypatch):
-    """Each tile shape the batched launch can pick (plain tiles and z-marched
-    strips) gives the traces of separate ib_forward calls, on shots whose sides
-    are not multiples of any tile."""
+    """Each tile shape the batched launch can pick (plain tiles, z-marched
+    strips of 64 x 8 tiles with one column per thread and of 64 x 16 tiles with
+    two) gives the traces of separate ib_forward calls, on shots whose sides
+    are not multiples of any tile; the second shot has an absorbing layer."""
     monkeypatch.setenv("IB_BATCH_SHAPE", str(shape))
     nt = 120
     shots, tables = [], []
@@ -347,21 +348,22 @@ def test_forward_batch_every_tile_shape(shape, monkeypatch):
         t = ib.ib_build_stencils(cuda(w["sdf"]), w["h"], "free", "second", w["M"])
         tables.append(t)
         shots.append(dict(vel=cuda(w["vel"], torch.float32), wavelet=cuda(w["wavelet"], torch.float32),
-                          src=cuda(w["src"]), rec=cuda(w["rec"]), w=w))
+                          src=cuda(w["src"]), rec=cuda(w["rec"]), w=w, damp=(12, 60.0) if k == 1 else None))
     dt = shots[0]["w"]["dt"]
     outs = ib.ib_forward_batch(tables, shots, dt, nt)
     ib.ib_sync_status()
     for t, sh, tr in zip(tables, shots, outs):
-        single = ib.ib_forward(t, sh["vel"], sh["wavelet"], sh["src"], sh["rec"], dt, nt)
+        single = ib.ib_forward(t, sh["vel"], sh["wavelet"], sh["src"], sh["rec"], dt, nt, damp=sh["damp"])
         ref = single.double().cpu().numpy()
         assert np.abs(ref).max() > 0
         assert rel_l2(tr.double().cpu().numpy(), ref) < 2e-6
 
 
 def test_forward_2d_strips_match_tiles(monkeypatch):
-    """The single-shot FP32 2D step on z-marched strips (IB_STRIP=1) gives the
-    traces of the 64 x 8 tile kernel (IB_STRIP=0), on a grid that is not a
-    multiple of the strip size."""
+    """The single-shot FP32 2D step on z-marched strips of 64 x 8 tiles
+    (IB_STRIP=1, IB_STRIP4=0) gives the traces of the 64 x 8 tile kernel
+    (IB_STRIP=0), on a grid that is not a multiple of the strip size."""
+    monkeypatch.setenv("IB_STRIP4", "0")
     w = inputs.workload_shot2d(30, nt=200, side=(150, 260))
     t = ib.ib_build_stencils(cuda(w["sdf"]), w["h"], "free", "second", w["M"])
     args = (t, cuda(w["vel"], torch.float32), cuda(w["wavelet"], torch.float32), cuda(w["src"]), cuda(w["rec"]),
@@ -370,6 +372,28 @@ def test_forward_2d_strips_match_tiles(monkeypatch):
     a = ib.ib_forward(*args).double().cpu().numpy()
     monkeypatch.setenv("IB_STRIP", "0")
     b = ib.ib_forward(*args).double().cpu().numpy()
+    assert np.abs(b).max() > 0
+    assert rel_l2(a, b) < 2e-6
+
+
+@pytest.mark.parametrize("damped", [False, True])
+def test_forward_2d_strip4_match_tiles(damped, monkeypatch):
+    """The single-shot FP32 2D step on strips of 64 x 16 tiles with two columns
+    per thread (IB_STRIP=1; the default strips) gives the traces of the 64 x 8
+    tile kernel (IB_STRIP=0), on a grid that is not a multiple of the strip
+    size, with and without the absorbing layer."""
+    w = inputs.workload_shot2d(30, nt=200, side=(150, 260))
+    t = ib.ib_build_stencils(cuda(w["sdf"]), w["h"], "free", "second", w["M"])
+    damp = (16, 60.0) if damped else None
+    args = (t, cuda(w["vel"], torch.float32), cuda(w["wavelet"], torch.float32), cuda(w["src"]), cuda(w["rec"]),
+            w["dt"], 200)
+    monkeypatch.setenv("IB_STRIP", "1")
+    monkeypatch.setenv("IB_STRIP4", "1")
+    a = ib.ib_forward(*args, damp=damp).double().cpu().numpy()
+    monkeypatch.setenv("IB_STRIP", "0")
+    monkeypatch.setenv("IB_STRIP4", "0")
+    b = ib.ib_forward(*args, damp=damp).double().cpu().numpy()
+    ib.ib_sync_status()
     assert np.abs(b).max() > 0
     assert rel_l2(a, b) < 2e-6
 
