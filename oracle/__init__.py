@@ -22,8 +22,10 @@ It is a plain, slow restatement of the paper, in the paper's order and notation:
                     the exact discrete adjoint of the leapfrog map.
 * ``images``     -- method-of-images analytic solutions for a flat surface.
 
-Parity of the modified stencils on curved geometry is pinned only through
-polynomial exactness and brute-force checks (see ``tests/test_oracle_*``);
-beyond that the oracle's curved-surface weights are "parity unpinned" against
-any external value: the paper prints none for a reproducible geometry.
+On curved geometry the modified stencils are pinned through polynomial
+exactness, brute-force checks, and exact solutions on a circle (harmonic fields
+that meet every imposed condition there): the truncation of the rows and the
+whole-field error converge at the extrapolation order (``tests/test_oracle_*``).
+No individual curved-surface weight is compared with an external value: the
+paper prints none for a reproducible geometry.
 """
