@@ -7,6 +7,7 @@ import pytest
 
 import bench
 
+
 def _w(shape, form="second"):
     return {"shape": shape, "form": form}
 
